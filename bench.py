@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark: complex multi-component LU GFLOPS (8 n^3 / 3 / t) at n = 4096.
+
+One step = one complex LU factorisation with partial pivoting (zgetrf) plus
+one solve (zgetrs) of a fresh copy of a synthetic n x n matrix (Gaussian
+leading limbs, canonical lower limbs, seed 1), i.e. one pass over the whole
+hot path.  value = steps * 8 n^3 / 3 / elapsed, summed over ranks (each rank
+an independent replica; the path has no data exchange).
+
+Timing: W untimed warm-up steps, then K steps between a barrier +
+torch.cuda.synchronize() on both sides, CUDA events on the library's stream,
+max over ranks.  The matrix (537 MB in DD) is larger than L2 (129 MB), so no
+explicit flush is needed.  SM clocks are sampled with nvidia-smi during the
+timed region.  `e2e` repeats the step through the C ABI with pinned host
+buffers: A and b are copied host->device and x device->host every step.
+
+--impl reference times the CPU oracle (test infrastructure, not the product)
+on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP64-pipe operations (DADD/DMUL/DFMA, 1 each) per complex multiply-accumulate
+# of the trailing update, as implemented in mc.cuh (leveled accumulator):
+# one real product-accumulate costs 12 (DD), 45 (TD), 112 (QD); 4M uses 4 per
+# complex MAC, 3M uses 3.
+I_REAL = {"dd": 12, "td": 45, "qd": 112}
+LIMBS = {"dd": 2, "td": 3, "qd": 4}
+# FP64 peak: 1.25 TFLOP/s nominal on GB300 counting an FMA as 2 flops, i.e.
+# 0.625e12 FP64 operations per second (2 per clock per SM at 2.07 GHz).
+FP64_OPS_PEAK = 0.625e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="mclu", choices=["mclu", "reference"])
+    p.add_argument("--prec", default="dd", choices=["dd", "td", "qd"])
+    p.add_argument("--method", default="4m", choices=["4m", "3m", "unblocked", "ozaki"])
+    p.add_argument("--n", type=int, default=4096)
+    p.add_argument("--nb", type=int, default=64)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle sample")
+    return p.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_inputs(n: int, L: int):
+    from paper_2403_16013_gb300 import inputs
+    A = inputs.gaussian_matrix(n, L, seed=1)
+    b = inputs.complex_gaussian_vector(n, L, seed=2)
+    return A, b
+
+
+def cpu_baseline(prec: str, target_s: float) -> dict:
+    """Time the oracle (unblocked GEPP + solve, as it stands) on the host cores on
+    a bounded sample: the largest n whose estimated run is about target_s."""
+    import oracle
+    L = LIMBS[prec]
+    cores = oracle.num_threads()
+    from paper_2403_16013_gb300 import inputs
+
+    def run(n):
+        A = inputs.gaussian_matrix(n, L, seed=1)
+        b = inputs.complex_gaussian_vector(n, L, seed=2)
+        t0 = time.perf_counter()
+        LU, ipiv, info, _ = oracle.zgetrf(A)
+        oracle.zgetrs(LU, ipiv, b)
+        return time.perf_counter() - t0
+
+    n0 = 96
+    t0 = run(n0)
+    n = int(n0 * (target_s / max(t0, 1e-3)) ** (1 / 3))
+    n = max(n0, min(n, 1024))
+    t = run(n) if n != n0 else t0
+    return {"value": 8 * n ** 3 / 3 / t / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"complex {prec.upper()} LU+solve n={n} (unblocked oracle, {t:.1f} s), seed 1",
+            "seconds": t}
+
+
+def run_reference(args):
+    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    per_step = max(3.0, args.cpu_seconds / 3)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(args.prec, per_step / 4)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.prec, per_step))
+    el = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": "complex DD/TD/QD LU GFLOPS (8n^3/3/t) at n=4096", "value": v,
+            "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"complex {args.prec.upper()} LU + solve (CPU oracle sample of the n={args.n} "
+                                   f"workload)", "n": args.n, "prec": args.prec},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    from paper_2403_16013_gb300 import api, binding, build
+    build.build()
+    binding.load()
+    n, L, prec = args.n, LIMBS[args.prec], args.prec
+    A_h, b_h = make_inputs(n, L)
+    A0 = torch.from_numpy(A_h).cuda()
+    b0 = torch.from_numpy(b_h).cuda()
+    A = torch.empty_like(A0)
+    x = torch.empty_like(b0)
+    ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    method = args.method
+
+    def step():
+        A.copy_(A0)
+        api.lu_factor_(A, ipiv, info, method=method, nb=args.nb)
+        x.copy_(b0)
+        api.lu_solve(A, ipiv, x, inplace=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if int(info.item()) != 0:
+        raise RuntimeError("singular benchmark matrix")
+
+    sampler = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.4)
+    binding.profile_begin(("gemm", "panel", "trsm", "laswp", "getrs", "other"))
+    launches0 = binding.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = binding.launch_count() - launches0
+    prof = binding.profile_end()
+    clocks = sampler.stop()
+    el_ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    flops = 8.0 * n ** 3 / 3.0
+    value = ws * args.steps * flops / (el_ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the trailing-update GEMM on the FP64 pipe
+    nb = args.nb
+    macs = 0
+    for j0 in range(0, n, nb):
+        jb = min(nb, n - j0)
+        n2 = n - j0 - jb
+        macs += n2 * n2 * jb
+    per_mac = (3 if method == "3m" else 4) * I_REAL[prec]
+    gemm_ms, gemm_calls = prof["gemm"]
+    roof = None
+    if gemm_calls and method in ("4m", "3m"):
+        per_launch_ops = macs * per_mac / (gemm_calls / args.steps)
+        achieved = per_launch_ops / (gemm_ms / gemm_calls * 1e-3)
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "T FP64-ops/s",
+                "frac": achieved / FP64_OPS_PEAK, "traffic": None,
+                "kernel": f"k_gemm<{L},{'3M' if method == '3m' else '4M'},beta>",
+                "ops_per_launch": per_launch_ops, "avg_launch_ms": gemm_ms / gemm_calls,
+                "share_of_step": gemm_ms / el_ms}
+
+    line = {"metric": "complex DD/TD/QD LU GFLOPS (8n^3/3/t) at n=4096", "value": value, "unit": "GFLOP/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"complex {prec.upper()} LU (zgetrf, partial pivoting) + solve (zgetrs), n={n}, "
+                                   f"nb={nb}, {method.upper()} trailing update, Gaussian limbs seed 1",
+                       "n": n, "prec": prec, "method": method, "nb": nb,
+                       "l2": "inputs larger than L2 (%.0f MB per matrix), no flush" % (A_h.nbytes / 1e6),
+                       "parallelism": f"replicas x{ws}"},
+            "gpu_launches": launches, "clocks": clocks, "roofline": roof,
+            "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+
+    if not args.no_e2e:
+        A_pin = torch.from_numpy(A_h).pin_memory()
+        b_pin = torch.from_numpy(b_h).pin_memory()
+        x_pin = torch.empty_like(b_pin).pin_memory()
+        ipiv_pin = torch.empty(n, dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            A.copy_(A_pin, non_blocking=True)
+            api.lu_factor_(A, ipiv, info, method=method, nb=args.nb)
+            x.copy_(b_pin, non_blocking=True)
+            api.lu_solve(A, ipiv, x, inplace=True)
+            x_pin.copy_(x, non_blocking=True)
+            ipiv_pin.copy_(ipiv, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        el = max_over_ranks(time.perf_counter() - t0, ws)
+        line["e2e"] = {"value": ws * max(1, args.steps) * flops / el / 1e9, "unit": "GFLOP/s",
+                       "h2d_bytes_per_step": A_h.nbytes + b_h.nbytes,
+                       "d2h_bytes_per_step": b_h.nbytes + 4 * n}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prec, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

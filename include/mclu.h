@@ -1,0 +1,172 @@
+/*
+ * mclu.h - C ABI of the GB300 (sm_103a) complex multi-component LU library.
+ *
+ * The library factors and solves complex linear systems A x = b (Sec. 3,
+ * Eq. (4) of Kouya, "Performance evaluation of accelerated complex
+ * multiple-precision LU decomposition") in double-double (DD, 2 limbs),
+ * triple-double (TD, 3 limbs) and quadruple-double (QD, 4 limbs) arithmetic:
+ * a real value is the unevaluated sum of L binary64 limbs (Sec. 1).
+ *
+ * Storage ("separate arrays for the real and imaginary parts", Sec. 2.2):
+ * a complex L-limb matrix with `rows` rows and `ncols` columns is 2*L
+ * column-major binary64 planes.  Plane (c, l), c = 0 real / 1 imaginary,
+ * l = 0..L-1 limb, starts at  base + (c*L + l) * ld * ncols, and element
+ * (i, j) of a plane is at offset j*ld + i.  Limbs must be ordered and
+ * nonoverlapping: |limb l+1| <= ulp(limb l).  Every result the library writes
+ * satisfies this; inputs with |limb l+1| <= ulp(limb l)/2 are canonical.
+ *
+ * Pointers: every matrix / vector / pivot pointer is a DEVICE pointer owned by
+ * the caller, unless a parameter says otherwise.  `stream` is a cudaStream_t
+ * passed as void* (NULL = legacy default stream).  Calls are asynchronous and
+ * stream-ordered: the return value only reports argument errors and launch
+ * failures; results are valid after the stream has been synchronised.  The
+ * library keeps no state between calls; workspace is allocated stream-ordered
+ * (cudaMallocAsync) inside each call and released before it returns.
+ *
+ * Return status: 0 = enqueued; -i = argument i (1-based) invalid, nothing
+ * enqueued; > 0 = a CUDA error code (cudaError_t) from a launch or allocation;
+ * MCLU_ERR_UNSUPPORTED = a valid request this build does not implement.
+ */
+#ifndef MCLU_H
+#define MCLU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MCLU_ERR_UNSUPPORTED 100000
+
+/* Trailing-update methods (Sec. 2.1 and Sec. 3). */
+enum {
+  MCLU_METHOD_4M = 0,        /* complex product by Eq. (1): four real products per complex MAC   */
+  MCLU_METHOD_3M = 1,        /* 3M matrix product by Eq. (3): T1, T2, T3 then Re = T1 - T2,      */
+                             /*   Im = T3 - (T1 + T2)                                              */
+  MCLU_METHOD_UNBLOCKED = 2, /* "Normal LU" of Sec. 3: right-looking row elimination, no GEMM    */
+  MCLU_METHOD_OZAKI = 3      /* Ozaki-scheme trailing update (Sec. 2.3): exact slice products    */
+};
+
+/* Optional parameters of the *_ex factorisation calls (NULL = defaults). */
+typedef struct mclu_opts {
+  int32_t nb;           /* panel width K of Sec. 3 (block size NDIM); 0 = 64; 1..256          */
+  int32_t method;       /* MCLU_METHOD_*; default MCLU_METHOD_4M                             */
+  int32_t ozaki_slices; /* slices per operand for MCLU_METHOD_OZAKI; 0 = precision default     */
+  int32_t reserved;     /* must be 0                                                          */
+} mclu_opts;
+
+/*
+ * zgetrf_{dd,td,qd}: LU factorisation with partial pivoting, P A = L U
+ * (Sec. 3: blocked right-looking LU with block size K, A22 <- A22 - L21 U12 by
+ * complex matrix multiplication, partial pivoting).
+ *   n     order of A (n >= 0)
+ *   A     device, n x n planes with leading dimension lda (plane stride
+ *         lda*n); overwritten by L (unit diagonal not stored) and U
+ *   lda   >= max(1, n)
+ *   ipiv  device int32[n]: 1-based pivot rows; row k was swapped with row
+ *         ipiv[k]-1, applied for k = 0..n-1 (LAPACK convention)
+ * Pivot key: cabs1(z) = |Re z| + |Im z| in L-limb arithmetic; ties go to the
+ * lowest row index.  A zero pivot does not stop the factorisation (use the
+ * _ex form to read info).  Default method: 4M, nb = 64.
+ */
+int zgetrf_dd(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream);
+int zgetrf_td(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream);
+int zgetrf_qd(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream);
+
+/*
+ * zgetrf_{dd,td,qd}_ex: as zgetrf_*, plus
+ *   info  device int32[1] or NULL: 0, or k+1 for the first exactly-zero pivot
+ *         U[k,k] (LAPACK convention)
+ *   opts  host pointer or NULL (defaults)
+ */
+int zgetrf_dd_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
+                 void *stream);
+int zgetrf_td_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
+                 void *stream);
+int zgetrf_qd_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
+                 void *stream);
+
+/*
+ * zgetrs_{dd,td,qd}: solve with the factors of zgetrf (Sec. 4: "forward and
+ * backward substitutions").
+ *   trans 'N': A X = B  (apply P, unit-lower forward, upper back substitution)
+ *         'C': A^H X = B (U^H forward, unit L^H back substitution, then P^T)
+ *   n, nrhs  >= 0
+ *   A, lda, ipiv  as returned by zgetrf (device, read only)
+ *   B     device, n x nrhs planes with leading dimension ldb (plane stride
+ *         ldb*nrhs); overwritten by X
+ */
+int zgetrs_dd(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda, const int32_t *ipiv, double *B,
+              int64_t ldb, void *stream);
+int zgetrs_td(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda, const int32_t *ipiv, double *B,
+              int64_t ldb, void *stream);
+int zgetrs_qd(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda, const int32_t *ipiv, double *B,
+              int64_t ldb, void *stream);
+
+/*
+ * zgemm_{dd,td,qd}: complex multi-component matrix product (Sec. 2.1,
+ * Eq. (1) for 4M and Eq. (3) for 3M; Sec. 2.3 for the Ozaki scheme).
+ *   beta_mode 0: C = A B;  1: C = C - A B (the trailing-update form)
+ *   method    MCLU_METHOD_4M, MCLU_METHOD_3M or MCLU_METHOD_OZAKI
+ *   A  m x k planes (lda, plane stride lda*k);  B  k x n planes (ldb, ldb*n);
+ *   C  m x n planes (ldc, ldc*n); all device.  C must not alias A or B.
+ */
+int zgemm_dd(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const double *A, int64_t lda,
+             const double *B, int64_t ldb, double *C, int64_t ldc, void *stream);
+int zgemm_td(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const double *A, int64_t lda,
+             const double *B, int64_t ldb, double *C, int64_t ldc, void *stream);
+int zgemm_qd(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const double *A, int64_t lda,
+             const double *B, int64_t ldb, double *C, int64_t ldc, void *stream);
+
+/*
+ * zadjoint_rank1_{dd,td,qd}: Abar = -lambda x^H, the matrix part of the
+ * adjoint of x = A^{-1} b (for lambda = A^{-H} xbar, computed by
+ * zgetrs_*('C', ...); the right-hand-side part is bbar = lambda).
+ *   lambda, x  device n x 1 planes (plane stride n)
+ *   Abar       device n x n planes, leading dimension ldab (plane stride ldab*n)
+ */
+int zadjoint_rank1_dd(int64_t n, const double *lambda, const double *x, double *Abar, int64_t ldab, void *stream);
+int zadjoint_rank1_td(int64_t n, const double *lambda, const double *x, double *Abar, int64_t ldab, void *stream);
+int zadjoint_rank1_qd(int64_t n, const double *lambda, const double *x, double *Abar, int64_t ldab, void *stream);
+
+/*
+ * mclu_vec_op: elementwise multi-component arithmetic on device vectors (the
+ * complex DD/TD/QD operations of Sec. 2.1-2.2: add, sub, mul, div, inv).
+ *   L      2, 3 or 4
+ *   op     real ops on limb-major arrays [L][count]:
+ *            0 add, 1 sub, 2 mul, 3 div
+ *          complex ops on plane arrays [2][L][count]:
+ *            10 add, 11 sub, 12 mul (4M, Eq. 1), 13 mul (3M, Eq. 2),
+ *            14 div, 15 inv (reciprocal), 16 cabs1 (result in the real part)
+ *   x, y   device inputs (y ignored by 15, 16); z device output
+ */
+int mclu_vec_op(int op, int L, int64_t count, const double *x, const double *y, double *z, void *stream);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all devices); a diagnostic for counting launches in a timed region. */
+uint64_t mclu_launch_count(void);
+
+/*
+ * Launch-class timing (diagnostic).  mclu_profile_begin(mask) makes every
+ * later call bracket its launches of the classes in `mask` (bit k = class k:
+ * 0 panel factorisation, 1 row swaps, 2 TRSM, 3 trailing-update / ZGEMM,
+ * 4 getrs, 5 other) with CUDA events recorded on the call's stream.
+ * mclu_profile_end synchronises those events and writes, for k < nkinds, the
+ * summed milliseconds ms[k] and the number of bracketed calls launches[k]
+ * (host arrays, either may be NULL), then stops recording.  Returns 0 or a
+ * CUDA error code.
+ */
+int mclu_profile_begin(uint32_t kind_mask);
+int mclu_profile_end(double *ms, int64_t *launches, int nkinds);
+
+/* Static description of a status code. */
+const char *mclu_status_string(int status);
+
+/* Library version as "major.minor.patch". */
+const char *mclu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCLU_H */

@@ -1,0 +1,389 @@
+// lu_host.cuh - host-side orchestration of the complex multi-component LU,
+// solve, ZGEMM and adjoint, templated on the limb count L.  Everything is
+// enqueued on the caller's stream with no host synchronisation; workspace is
+// allocated stream-ordered and freed at the end of each call.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "../../include/mclu.h"
+#include "lu_kernels.cuh"
+
+namespace mclu {
+
+#define MCLU_TRY(expr)                         \
+  do {                                         \
+    cudaError_t e_ = (expr);                   \
+    if (e_ != cudaSuccess) return (int)e_;     \
+  } while (0)
+// Every kernel launch is followed by MCLU_LAUNCHED(): it counts the launch
+// (mclu_launch_count) and reports a failed launch as the CUDA error code.
+void note_launch();
+#define MCLU_LAUNCHED()            \
+  do {                             \
+    note_launch();                 \
+    MCLU_TRY(cudaGetLastError());  \
+  } while (0)
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Launch classes timed by mclu_profile_begin / mclu_profile_end.
+enum ProfKind { PK_PANEL = 0, PK_LASWP = 1, PK_TRSM = 2, PK_GEMM = 3, PK_SOLVE = 4, PK_OTHER = 5, PK_COUNT = 6 };
+bool prof_on(int kind);
+void prof_push(int kind, cudaEvent_t e0, cudaEvent_t e1);
+
+// Brackets the launches of one class with CUDA events on their stream when
+// profiling of that class is enabled (no cost otherwise).
+struct ProfScope {
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(int k, cudaStream_t st) : kind(k), s(st) {
+    if (prof_on(kind) && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, s);
+  }
+  ~ProfScope() {
+    if (!e0) return;
+    cudaEvent_t e1;
+    if (cudaEventCreate(&e1) == cudaSuccess) {
+      cudaEventRecord(e1, s);
+      prof_push(kind, e0, e1);
+    } else {
+      cudaEventDestroy(e0);
+    }
+  }
+};
+
+// Stream-ordered workspace that is released on every exit path.
+struct Workspace {
+  void *p = nullptr;
+  cudaStream_t s = nullptr;
+  ~Workspace() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  cudaError_t alloc(size_t bytes, cudaStream_t st) {
+    s = st;
+    return cudaMallocAsync(&p, bytes < 256 ? 256 : bytes, st);
+  }
+};
+
+struct Carver {  // 256-byte aligned sub-allocations of one workspace block
+  char *base;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t count) {
+    size_t bytes = ((count * sizeof(T)) + 255) & ~(size_t)255;
+    T *r = reinterpret_cast<T *>(base + off);
+    off += bytes;
+    return r;
+  }
+};
+
+template <int L>
+size_t getrf_ws_bytes(int64_t n, int nb, bool m3) {
+  size_t nparts = (size_t)cdiv(std::max<int64_t>(n, 1), PANEL_T) + 1;
+  size_t b = 4 * 256;                                           // counter, info, zflag, recip
+  b += ((nparts * L * sizeof(double)) + 255) & ~(size_t)255;   // part_key
+  b += ((nparts * sizeof(int)) + 255) & ~(size_t)255;          // part_idx
+  b += ((2 * 2 * L * (size_t)n * sizeof(double)) + 255) & ~(size_t)255;  // lbuf
+  if (m3) b += 2 * (((size_t)n * nb * L * sizeof(double)) + 255);         // 3M pre-sums
+  return b + 1024;
+}
+
+template <int L>
+int launch_gemm(int method, bool beta, View A, View B, View C, View SA, View SB, int64_t m, int64_t n, int64_t k,
+                cudaStream_t s) {
+  if (m <= 0 || n <= 0) return 0;
+  dim3 grid((unsigned)cdiv(m, GEMM_T), (unsigned)cdiv(n, GEMM_T)), block(GEMM_T, GEMM_T);
+  if (method == MCLU_METHOD_3M) {
+    if (beta)
+      k_gemm<L, true, true><<<grid, block, 0, s>>>(A, B, C, SA, SB, m, n, k);
+    else
+      k_gemm<L, true, false><<<grid, block, 0, s>>>(A, B, C, SA, SB, m, n, k);
+  } else {
+    if (beta)
+      k_gemm<L, false, true><<<grid, block, 0, s>>>(A, B, C, SA, SB, m, n, k);
+    else
+      k_gemm<L, false, false><<<grid, block, 0, s>>>(A, B, C, SA, SB, m, n, k);
+  }
+  MCLU_LAUNCHED();
+  return 0;
+}
+
+template <int L>
+int launch_resum(View X, View S, int64_t m, int64_t k, cudaStream_t s) {
+  int64_t tot = m * k;
+  if (tot <= 0) return 0;
+  k_resum<L><<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(X, S, m, k);
+  MCLU_LAUNCHED();
+  return 0;
+}
+
+// Right-looking blocked LU (Sec. 3): for each panel of width nb: factor the
+// panel (pivot search, swap, scale, rank-1 steps), swap the rows left and
+// right of it, TRSM for U12, and the trailing update A22 <- A22 - L21 U12.
+template <int L>
+int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
+          cudaStream_t s) {
+  if (n < 0) return -1;
+  if (n > 0 && Ap == nullptr) return -2;
+  if (lda < std::max<int64_t>(1, n)) return -3;
+  if (n > 0 && ipiv == nullptr) return -4;
+  int nb = 64, method = MCLU_METHOD_4M;
+  if (opts) {
+    if (opts->nb < 0 || opts->nb > 256) return -6;
+    if (opts->nb) nb = opts->nb;
+    if (opts->method < MCLU_METHOD_4M || opts->method > MCLU_METHOD_OZAKI) return -6;
+    method = opts->method;
+    if (method == MCLU_METHOD_OZAKI) return MCLU_ERR_UNSUPPORTED;
+    if (opts->reserved != 0) return -6;
+  }
+  if (n > INT32_MAX - 1) return -1;
+  if (n == 0) {
+    if (info) MCLU_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
+    return 0;
+  }
+  if (method == MCLU_METHOD_UNBLOCKED) nb = (int)std::min<int64_t>(n, INT32_MAX);
+  const bool m3 = method == MCLU_METHOD_3M;
+  Workspace w;
+  MCLU_TRY(w.alloc(getrf_ws_bytes<L>(n, m3 ? nb : 0, m3), s));
+  Carver cv{(char *)w.p};
+  PanelWS<L> ws;
+  char *hdr = cv.take<char>(4 * 256);
+  ws.counter = (int *)hdr;
+  ws.info = (int *)(hdr + 256);
+  ws.zflag = (int *)(hdr + 512);
+  ws.recip = (double *)(hdr + 768);
+  size_t nparts = (size_t)cdiv(n, PANEL_T) + 1;
+  ws.part_key = cv.take<double>(nparts * L);
+  ws.part_idx = cv.take<int>(nparts);
+  ws.lbuf = cv.take<double>(2 * 2 * L * (size_t)n);
+  ws.lbuf_ld = n;
+  double *sumL = nullptr, *sumU = nullptr;
+  if (m3) {
+    sumL = cv.take<double>((size_t)n * nb * L);
+    sumU = cv.take<double>((size_t)n * nb * L);
+  }
+  MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
+  View A{Ap, lda, lda * n};
+
+  for (int64_t j0 = 0; j0 < n; j0 += nb) {
+    const int64_t jb = std::min<int64_t>(nb, n - j0), jend = j0 + jb;
+    {  // panel: rows [j0, n), columns [j0, jend)
+      ProfScope ps(PK_PANEL, s);
+      k_pivot_first<L><<<(unsigned)cdiv(n - j0, SEARCH_T), SEARCH_T, 0, s>>>(A, n, j0, j0, jend, ipiv, ws);
+      MCLU_LAUNCHED();
+      for (int64_t j = j0; j < jend; j++) {
+        dim3 grid((unsigned)std::max<int64_t>(1, cdiv(n - j - 1, PANEL_T)), (unsigned)panel_colblocks(j, jend));
+        k_panel_step<L><<<grid, dim3(PANEL_T, PANEL_T), 0, s>>>(A, n, j, j0, jend, ipiv, ws);
+        MCLU_LAUNCHED();
+      }
+    }
+    if (j0 > 0) {  // apply the panel's swaps to the columns on its left
+      ProfScope ps(PK_LASWP, s);
+      k_laswp<L><<<(unsigned)cdiv(j0 * 2 * L, 256), 256, 0, s>>>(A, 0, j0, j0, jend, ipiv);
+      MCLU_LAUNCHED();
+    }
+    if (jend < n) {
+      const int64_t n2 = n - jend;
+      {  // ... and on its right
+        ProfScope ps(PK_LASWP, s);
+        k_laswp<L><<<(unsigned)cdiv(n2 * 2 * L, 256), 256, 0, s>>>(A, jend, n, j0, jend, ipiv);
+        MCLU_LAUNCHED();
+      }
+      {  // U12 = L11^{-1} A12
+        ProfScope ps(PK_TRSM, s);
+        const int RT = (int)((jb + 31) / 32 * 32);
+        const int CT = std::max(1, 256 / RT);
+        View A12{Ap + jend * lda, lda, lda * n};
+        k_tri_block<L, true, true, false>
+            <<<(unsigned)cdiv(n2, CT), dim3(RT, CT), CT * 2 * L * sizeof(double), s>>>(A, j0, (int)jb, A12, n2);
+        MCLU_LAUNCHED();
+      }
+      // A22 -= L21 U12
+      View L21{Ap + j0 * lda + jend, lda, lda * n};
+      View U12{Ap + jend * lda + j0, lda, lda * n};
+      View A22{Ap + jend * lda + jend, lda, lda * n};
+      View SL{nullptr, 0, 0}, SU{nullptr, 0, 0};
+      if (m3) {
+        ProfScope ps(PK_OTHER, s);
+        SL = View{sumL, n2, n2 * jb};
+        SU = View{sumU, jb, jb * n2};
+        int rc = launch_resum<L>(L21, SL, n2, jb, s);
+        if (rc) return rc;
+        rc = launch_resum<L>(U12, SU, jb, n2, s);
+        if (rc) return rc;
+      }
+      ProfScope ps(PK_GEMM, s);
+      int rc = launch_gemm<L>(method, true, L21, U12, A22, SL, SU, n2, n2, jb, s);
+      if (rc) return rc;
+    }
+  }
+  if (info) MCLU_TRY(cudaMemcpyAsync(info, ws.info, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  return 0;
+}
+
+// Forward (LOWER) or backward substitution over all diagonal blocks of T on
+// the n x nrhs planes X.
+template <int L, bool LOWER, bool UNIT, bool CONJT>
+int tri_solve(View A, int64_t n, View X, int64_t nrhs, cudaStream_t s) {
+  constexpr int BS = 32;
+  const int64_t nblk = cdiv(n, BS);
+  for (int64_t q = 0; q < nblk; q++) {
+    const int64_t b = LOWER ? q : nblk - 1 - q;
+    const int64_t k0 = b * BS;
+    const int bs = (int)std::min<int64_t>(BS, n - k0);
+    const int CT = 8;
+    k_tri_block<L, LOWER, UNIT, CONJT>
+        <<<(unsigned)cdiv(nrhs, CT), dim3(BS, CT), CT * 2 * L * sizeof(double), s>>>(A, k0, bs, X, nrhs);
+    MCLU_LAUNCHED();
+    const int64_t r0 = LOWER ? k0 + bs : 0, r1 = LOWER ? n : k0;
+    if (r1 > r0) {
+      dim3 grid((unsigned)cdiv(r1 - r0, 32), (unsigned)cdiv(nrhs, 8));
+      k_gemv<L, CONJT><<<grid, dim3(32, 8), 0, s>>>(A, r0, r1, k0, bs, X, nrhs);
+      MCLU_LAUNCHED();
+    }
+  }
+  return 0;
+}
+
+template <int L>
+int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, const int32_t *ipiv, double *Bp,
+          int64_t ldb, cudaStream_t s) {
+  if (trans != 'N' && trans != 'n' && trans != 'C' && trans != 'c') return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0) return -3;
+  if (n > 0 && Ap == nullptr) return -4;
+  if (lda < std::max<int64_t>(1, n)) return -5;
+  if (n > 0 && ipiv == nullptr) return -6;
+  if (n > 0 && nrhs > 0 && Bp == nullptr) return -7;
+  if (ldb < std::max<int64_t>(1, n)) return -8;
+  if (n == 0 || nrhs == 0) return 0;
+  if (n > INT32_MAX - 1) return -2;
+  const bool conj = (trans == 'C' || trans == 'c');
+  ProfScope ps(PK_SOLVE, s);
+  View A{const_cast<double *>(Ap), lda, lda * n};
+  View B{Bp, ldb, ldb * nrhs};
+  Workspace w;
+  const size_t perm_bytes = ((size_t)n * sizeof(int32_t) + 255) & ~(size_t)255;
+  MCLU_TRY(w.alloc(perm_bytes + (size_t)2 * L * n * nrhs * sizeof(double), s));
+  int32_t *perm = (int32_t *)w.p;
+  View X{(double *)((char *)w.p + perm_bytes), n, n * nrhs};
+  const size_t smem_perm = (size_t)n * sizeof(int32_t);
+  const int use_smem = smem_perm <= 200 * 1024 ? 1 : 0;
+  if (use_smem) MCLU_TRY(cudaFuncSetAttribute(k_perm_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  k_perm_build<<<1, 32, use_smem ? smem_perm : 0, s>>>(ipiv, n, perm, use_smem);
+  MCLU_LAUNCHED();
+  const unsigned pg = (unsigned)cdiv(n * nrhs, 256);
+  if (!conj) {
+    k_permute<L><<<pg, 256, 0, s>>>(B, X, perm, n, nrhs, 0);  // X = P B
+    MCLU_LAUNCHED();
+    int rc = tri_solve<L, true, true, false>(A, n, X, nrhs, s);
+    if (rc) return rc;
+    rc = tri_solve<L, false, false, false>(A, n, X, nrhs, s);
+    if (rc) return rc;
+    MCLU_TRY(cudaMemcpy2DAsync(Bp, ldb * sizeof(double), X.p, n * sizeof(double), n * sizeof(double),
+                               (size_t)2 * L * nrhs, cudaMemcpyDeviceToDevice, s));
+  } else {
+    MCLU_TRY(cudaMemcpy2DAsync(X.p, n * sizeof(double), Bp, ldb * sizeof(double), n * sizeof(double),
+                               (size_t)2 * L * nrhs, cudaMemcpyDeviceToDevice, s));
+    int rc = tri_solve<L, true, false, true>(A, n, X, nrhs, s);  // U^H w = b
+    if (rc) return rc;
+    rc = tri_solve<L, false, true, true>(A, n, X, nrhs, s);      // L^H z = w
+    if (rc) return rc;
+    k_permute<L><<<pg, 256, 0, s>>>(X, B, perm, n, nrhs, 1);     // B = P^T z
+    MCLU_LAUNCHED();
+  }
+  return 0;
+}
+
+template <int L>
+int gemm(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const double *Ap, int64_t lda, const double *Bp,
+         int64_t ldb, double *Cp, int64_t ldc, cudaStream_t s) {
+  if (beta_mode != 0 && beta_mode != 1) return -1;
+  if (method != MCLU_METHOD_4M && method != MCLU_METHOD_3M && method != MCLU_METHOD_OZAKI) return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  if (m > 0 && k > 0 && Ap == nullptr) return -6;
+  if (lda < std::max<int64_t>(1, m)) return -7;
+  if (k > 0 && n > 0 && Bp == nullptr) return -8;
+  if (ldb < std::max<int64_t>(1, k)) return -9;
+  if (m > 0 && n > 0 && Cp == nullptr) return -10;
+  if (ldc < std::max<int64_t>(1, m)) return -11;
+  if (m == 0 || n == 0) return 0;
+  if (method == MCLU_METHOD_OZAKI) return MCLU_ERR_UNSUPPORTED;
+  View A{const_cast<double *>(Ap), lda, lda * k}, B{const_cast<double *>(Bp), ldb, ldb * n}, C{Cp, ldc, ldc * n};
+  View SA{nullptr, 0, 0}, SB{nullptr, 0, 0};
+  Workspace w;
+  if (method == MCLU_METHOD_3M && k > 0) {
+    MCLU_TRY(w.alloc((size_t)(m * k + k * n) * L * sizeof(double) + 512, s));
+    SA = View{(double *)w.p, m, m * k};
+    SB = View{(double *)w.p + m * k * L, k, k * n};
+    int rc = launch_resum<L>(A, SA, m, k, s);
+    if (rc) return rc;
+    rc = launch_resum<L>(B, SB, k, n, s);
+    if (rc) return rc;
+  }
+  ProfScope ps(PK_GEMM, s);
+  return launch_gemm<L>(method, beta_mode == 1, A, B, C, SA, SB, m, n, k, s);
+}
+
+template <int L>
+int adjoint_rank1(int64_t n, const double *lam, const double *x, double *Ab, int64_t ldab, cudaStream_t s) {
+  if (n < 0) return -1;
+  if (n > 0 && (lam == nullptr)) return -2;
+  if (n > 0 && (x == nullptr)) return -3;
+  if (n > 0 && (Ab == nullptr)) return -4;
+  if (ldab < std::max<int64_t>(1, n)) return -5;
+  if (n == 0) return 0;
+  if (n > 65535) return -1;
+  View vl{const_cast<double *>(lam), n, n}, vx{const_cast<double *>(x), n, n}, vA{Ab, ldab, ldab * n};
+  k_rank1_adjoint<L><<<dim3((unsigned)cdiv(n, 256), (unsigned)n), 256, 0, s>>>(vl, vx, vA, n);
+  MCLU_LAUNCHED();
+  return 0;
+}
+
+template <int L>
+int vec_op(int op, int64_t count, const double *x, const double *y, double *z, cudaStream_t s) {
+  const bool real = op >= 0 && op <= 3;
+  const bool cplx = op >= 10 && op <= 16;
+  if (!real && !cplx) return -1;
+  if (count < 0) return -3;
+  if (count == 0) return 0;
+  if (!x) return -4;
+  if (!y && op != 15 && op != 16) return -5;
+  if (!z) return -6;
+  k_vec_op<L><<<(unsigned)cdiv(count, 128), 128, 0, s>>>(op, count, x, y, z);
+  MCLU_LAUNCHED();
+  return 0;
+}
+
+}  // namespace mclu
+
+// One translation unit per precision defines the C entry points.
+#define MCLU_DEFINE_PRECISION(SUF, LIMBS)                                                                        \
+  extern "C" int zgetrf_##SUF##_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info,             \
+                                   const mclu_opts *opts, void *stream) {                                       \
+    return mclu::getrf<LIMBS>(n, A, lda, ipiv, info, opts, (cudaStream_t)stream);                               \
+  }                                                                                                              \
+  extern "C" int zgetrf_##SUF(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream) {                 \
+    return mclu::getrf<LIMBS>(n, A, lda, ipiv, nullptr, nullptr, (cudaStream_t)stream);                         \
+  }                                                                                                              \
+  extern "C" int zgetrs_##SUF(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda,                \
+                              const int32_t *ipiv, double *B, int64_t ldb, void *stream) {                      \
+    return mclu::getrs<LIMBS>(trans, n, nrhs, A, lda, ipiv, B, ldb, (cudaStream_t)stream);                      \
+  }                                                                                                              \
+  extern "C" int zgemm_##SUF(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const double *A,       \
+                             int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc, void *stream) { \
+    return mclu::gemm<LIMBS>(beta_mode, method, m, n, k, A, lda, B, ldb, C, ldc, (cudaStream_t)stream);        \
+  }                                                                                                              \
+  extern "C" int zadjoint_rank1_##SUF(int64_t n, const double *lambda, const double *x, double *Abar,           \
+                                      int64_t ldab, void *stream) {                                             \
+    return mclu::adjoint_rank1<LIMBS>(n, lambda, x, Abar, ldab, (cudaStream_t)stream);                          \
+  }                                                                                                              \
+  int mclu_vec_op_##SUF(int op, int64_t count, const double *x, const double *y, double *z, void *stream) {     \
+    return mclu::vec_op<LIMBS>(op, count, x, y, z, (cudaStream_t)stream);                                       \
+  }

@@ -1,0 +1,663 @@
+// lu_kernels.cuh - CUDA kernels of the complex multi-component LU (Sec. 3) and
+// solve (Sec. 4), templated on the limb count L (2 DD, 3 TD, 4 QD).
+//
+// All arithmetic is on the FP64 pipe through mc.cuh.  On GB300 the FP64 pipe
+// is the scarce unit (about 1.6 results per clock per SM, against ~110 for
+// FP32), so every kernel here is sized for FP64 issue, not for bandwidth:
+// enough independent elements per SM to keep the FP64 pipe busy, operands
+// staged in shared memory once per tile, no redundant multi-component work.
+//
+// Pivoting (partial pivoting of Sec. 3): the key is cabs1 = |Re| + |Im| in
+// L-limb arithmetic, compared lexicographically on the renormalised limbs
+// (integer compares); ties go to the lowest row.  A column's search spans
+// many CTAs: each writes a partial (key, row); the CTA that arrives last on an
+// atomic counter (threadfence-reduction pattern, no waiting anywhere) reduces
+// the partials, swaps the pivot row inside the panel, records ipiv and info,
+// and leaves the reciprocal of the pivot for the next launch.
+#pragma once
+
+#include <climits>
+
+#include "mc.cuh"
+
+namespace mclu {
+
+constexpr int PANEL_T = 16;   // panel-step CTA: 16 rows x 16 columns of the panel
+constexpr int SEARCH_T = 256; // threads of a pivot-search CTA
+constexpr int GEMM_T = 16;    // GEMM CTA tile: 16 x 16 outputs, k staged 16 at a time
+
+// Workspace shared by the panel kernels of one factorisation.
+template <int L>
+struct PanelWS {
+  int *counter;     // arrival counter of the last-CTA pattern (reset by the last CTA)
+  int *info;        // first zero pivot, 1-based (0 = none)
+  int *zflag;       // 1 if the current pivot column was entirely zero
+  double *recip;    // [2L] reciprocal of the current pivot (re limbs, im limbs)
+  double *part_key; // [nparts][L]
+  int *part_idx;    // [nparts]
+  double *lbuf;     // [2][2L][lbuf_ld] pending multipliers of a column (double buffered)
+  int64_t lbuf_ld;
+};
+
+template <int L>
+__device__ __forceinline__ bool better(const R<L> &ka, int ia, const R<L> &kb, int ib) {
+  if (r_gt<L>(ka, kb)) return true;
+  if (r_gt<L>(kb, ka)) return false;
+  return ia < ib;
+}
+
+// Block-wide argmax; nthr is a power of two; result in (key, idx) of thread 0.
+template <int L>
+__device__ void block_argmax(R<L> &key, int &idx, int tid, int nthr) {
+  __shared__ double s_key[SEARCH_T * L];
+  __shared__ int s_idx[SEARCH_T];
+#pragma unroll
+  for (int l = 0; l < L; l++) s_key[tid * L + l] = key.x[l];
+  s_idx[tid] = idx;
+  __syncthreads();
+  for (int s = nthr / 2; s > 0; s >>= 1) {
+    if (tid < s) {
+      R<L> a, b;
+#pragma unroll
+      for (int l = 0; l < L; l++) {
+        a.x[l] = s_key[tid * L + l];
+        b.x[l] = s_key[(tid + s) * L + l];
+      }
+      int ia = s_idx[tid], ib = s_idx[tid + s];
+      if (better<L>(b, ib, a, ia)) {
+#pragma unroll
+        for (int l = 0; l < L; l++) s_key[tid * L + l] = b.x[l];
+        s_idx[tid] = ib;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+#pragma unroll
+    for (int l = 0; l < L; l++) key.x[l] = s_key[l];
+    idx = s_idx[0];
+  }
+  __syncthreads();
+}
+
+template <int L>
+__device__ __forceinline__ R<L> invalid_key() {
+  R<L> k = r_zero<L>();
+  k.x[0] = -1.0;
+  return k;
+}
+
+// Last-CTA finalisation of the pivot of column jp: reduce nparts partials,
+// record ipiv/info, swap rows jp <-> p over panel columns [j0, jend) (and the
+// pending multipliers of column jcol in lbuf slot `pend` if pend >= 0), then
+// compute the reciprocal of the new pivot.
+template <int L>
+__device__ void finalize_pivot(View A, int64_t n, int64_t jp, int64_t j0, int64_t jend, int32_t *ipiv,
+                               PanelWS<L> ws, int nparts, int pend, int tid, int nthr) {
+  R<L> key = invalid_key<L>();
+  int idx = INT_MAX;
+  for (int q = tid; q < nparts; q += nthr) {
+    R<L> k;
+#pragma unroll
+    for (int l = 0; l < L; l++) k.x[l] = __ldcg(ws.part_key + (int64_t)q * L + l);
+    int i = __ldcg(ws.part_idx + q);
+    if (better<L>(k, i, key, idx)) {
+      key = k;
+      idx = i;
+    }
+  }
+  block_argmax<L>(key, idx, tid, nthr);
+  __shared__ int s_p, s_zero;
+  if (tid == 0) {
+    bool zero = !(key.x[0] > 0.0);
+    int64_t p = (idx == INT_MAX || zero) ? jp : idx;
+    s_p = (int)p;
+    s_zero = zero ? 1 : 0;
+    ipiv[jp] = (int32_t)(p + 1);
+    *ws.zflag = zero ? 1 : 0;
+    if (zero && *ws.info == 0) *ws.info = (int)(jp + 1);
+  }
+  __syncthreads();
+  const int64_t p = s_p;
+  if (p != jp) {
+    const int64_t w = jend - j0;
+    for (int64_t t = tid; t < w * 2 * L; t += nthr) {
+      int64_t c = j0 + t / (2 * L);
+      int pl = (int)(t % (2 * L));
+      double *P = A.p + (int64_t)pl * A.ps + c * A.ld;
+      double a = P[jp], b = P[p];
+      P[jp] = b;
+      P[p] = a;
+    }
+    if (pend >= 0) {
+      for (int pl = tid; pl < 2 * L; pl += nthr) {
+        double *P = ws.lbuf + ((int64_t)pend * 2 * L + pl) * ws.lbuf_ld;
+        double a = P[jp], b = P[p];
+        P[jp] = b;
+        P[p] = a;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (!s_zero) {
+      Z<L> r = z_inv<L>(ldz<L>(A, jp, jp));
+#pragma unroll
+      for (int l = 0; l < L; l++) {
+        ws.recip[l] = r.re.x[l];
+        ws.recip[L + l] = r.im.x[l];
+      }
+    }
+    *ws.counter = 0;
+    __threadfence();
+  }
+}
+
+// True in exactly one CTA per launch: the last one to arrive.
+__device__ __forceinline__ bool arrive_last(int *counter, int nblocks, int tid) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    int prev = atomicAdd(counter, 1);
+    s_last = (prev == nblocks - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// Pivot search of column j over rows [j, n) (first column of a panel).
+template <int L>
+__global__ void __launch_bounds__(SEARCH_T) k_pivot_first(View A, int64_t n, int64_t j, int64_t j0, int64_t jend,
+                                                          int32_t *ipiv, PanelWS<L> ws) {
+  const int tid = threadIdx.x;
+  const int64_t i = j + (int64_t)blockIdx.x * SEARCH_T + tid;
+  R<L> key = invalid_key<L>();
+  int idx = INT_MAX;
+  if (i < n) {
+    key = pivot_key<L>(ldz<L>(A, i, j));
+    idx = (int)i;
+  }
+  block_argmax<L>(key, idx, tid, SEARCH_T);
+  if (tid == 0) {
+#pragma unroll
+    for (int l = 0; l < L; l++) ws.part_key[(int64_t)blockIdx.x * L + l] = key.x[l];
+    ws.part_idx[blockIdx.x] = idx;
+  }
+  if (arrive_last(ws.counter, gridDim.x, tid))
+    finalize_pivot<L>(A, n, j, j0, jend, ipiv, ws, gridDim.x, -1, tid, SEARCH_T);
+}
+
+__host__ __device__ __forceinline__ int panel_colblocks(int64_t j, int64_t jend) {
+  int64_t c = jend - j - 1;
+  return c <= 0 ? 1 : (int)((c + PANEL_T - 1) / PANEL_T);
+}
+
+// One column step of the panel [j0, jend): scale column j by the pivot's
+// reciprocal (multipliers l_i, Sec. 3 / the paper's "inv" operation), update
+// the panel columns j+1..jend-1 (A_ic -= l_i A_jc), and search the pivot of
+// column j+1.  Grid: (row blocks of rows j+1..n-1, column blocks).
+template <int L>
+__global__ void __launch_bounds__(PANEL_T *PANEL_T)
+    k_panel_step(View A, int64_t n, int64_t j, int64_t j0, int64_t jend, int32_t *ipiv, PanelWS<L> ws) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * PANEL_T + tx;
+  const int64_t i = j + 1 + (int64_t)blockIdx.x * PANEL_T + tx;
+  const bool row_ok = i < n;
+  const bool via_lbuf = gridDim.y > 1;
+  const int slot = (int)(j & 1);
+  __shared__ double s_l[PANEL_T][2 * L];
+  __shared__ double s_u[PANEL_T][2 * L];
+  const int zero = *ws.zflag;
+
+  // flush the multipliers of column j-1 if they were left in lbuf
+  if (j > j0 && panel_colblocks(j - 1, jend) > 1 && blockIdx.y == 0 && ty == 1) {
+    const int ps = 1 - slot;
+    const int64_t fi = i;
+    if (fi < n) {
+#pragma unroll
+      for (int pl = 0; pl < 2 * L; pl++)
+        A.p[(int64_t)pl * A.ps + (j - 1) * A.ld + fi] = ws.lbuf[((int64_t)ps * 2 * L + pl) * ws.lbuf_ld + fi];
+    }
+    if (blockIdx.x == 0 && tx == 0) {  // row j, not in this launch's row range
+#pragma unroll
+      for (int pl = 0; pl < 2 * L; pl++)
+        A.p[(int64_t)pl * A.ps + (j - 1) * A.ld + j] = ws.lbuf[((int64_t)ps * 2 * L + pl) * ws.lbuf_ld + j];
+    }
+  }
+
+  // multipliers of this CTA's rows
+  if (ty == 0) {
+    Z<L> l = z_zero<L>();
+    if (row_ok) {
+      Z<L> a = ldz<L>(A, i, j);
+      if (zero) {
+        l = a;
+      } else {
+        Z<L> r;
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          r.re.x[q] = ws.recip[q];
+          r.im.x[q] = ws.recip[L + q];
+        }
+        l = z_mul<L>(a, r);
+      }
+      if (!via_lbuf) {
+        stz<L>(A, i, j, l);
+      } else if (blockIdx.y == 0) {
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          ws.lbuf[((int64_t)slot * 2 * L + q) * ws.lbuf_ld + i] = l.re.x[q];
+          ws.lbuf[((int64_t)slot * 2 * L + L + q) * ws.lbuf_ld + i] = l.im.x[q];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      s_l[tx][q] = l.re.x[q];
+      s_l[tx][L + q] = l.im.x[q];
+    }
+  }
+  // pivot-row entries of this CTA's columns
+  const int64_t cbase = j + 1 + (int64_t)blockIdx.y * PANEL_T;
+  if (ty == 1 && cbase + tx < jend) {
+    Z<L> u = ldz<L>(A, j, cbase + tx);
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      s_u[tx][q] = u.re.x[q];
+      s_u[tx][L + q] = u.im.x[q];
+    }
+  }
+  __syncthreads();
+
+  const int64_t c = cbase + ty;
+  Z<L> updated;
+  if (row_ok && c < jend && !zero) {
+    Z<L> l, u;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      l.re.x[q] = s_l[tx][q];
+      l.im.x[q] = s_l[tx][L + q];
+      u.re.x[q] = s_u[ty][q];
+      u.im.x[q] = s_u[ty][L + q];
+    }
+    updated = z_fms<L>(ldz<L>(A, i, c), l, u);
+    stz<L>(A, i, c, updated);
+  } else if (row_ok && c < jend) {
+    updated = ldz<L>(A, i, c);
+  }
+
+  // pivot search of column j+1 (CTAs of column block 0, threads ty == 0)
+  const bool search = (j + 1 < jend);
+  if (search) {
+    if (blockIdx.y == 0) {
+      R<L> key = invalid_key<L>();
+      int idx = INT_MAX;
+      if (ty == 0 && row_ok) {
+        key = pivot_key<L>(updated);
+        idx = (int)i;
+      }
+      block_argmax<L>(key, idx, tid, PANEL_T * PANEL_T);
+      if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < L; q++) ws.part_key[(int64_t)blockIdx.x * L + q] = key.x[q];
+        ws.part_idx[blockIdx.x] = idx;
+      }
+    }
+    if (arrive_last(ws.counter, gridDim.x * gridDim.y, tid))
+      finalize_pivot<L>(A, n, j + 1, j0, jend, ipiv, ws, gridDim.x, via_lbuf ? slot : -1, tid, PANEL_T * PANEL_T);
+  }
+}
+
+// Apply the row swaps ipiv[k0..k1) to columns [c0, c1) (all 2L planes).
+template <int L>
+__global__ void k_laswp(View A, int64_t c0, int64_t c1, int64_t k0, int64_t k1, const int32_t *ipiv) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ncols = c1 - c0;
+  if (t >= ncols * 2 * L) return;
+  const int64_t c = c0 + t % ncols;
+  const int pl = (int)(t / ncols);
+  double *P = A.p + (int64_t)pl * A.ps + c * A.ld;
+  for (int64_t k = k0; k < k1; k++) {
+    int64_t p = ipiv[k] - 1;
+    if (p != k) {
+      double a = P[k], b = P[p];
+      P[k] = b;
+      P[p] = a;
+    }
+  }
+}
+
+// Triangular block solve T x = b for the bs x bs diagonal block of A at
+// (k0, k0) on columns of X (rows k0..k0+bs-1).  T = A (LOWER: unit or not) or,
+// with CONJT, T(r, k) = conj(A(k0+k, k0+r)).  Right-looking inside the block:
+// at step k the owner of row k finalises x_k (dividing by T_kk if !UNIT) and
+// every row below (LOWER) or above (!LOWER) subtracts T(r,k) x_k.
+// Block: (RT rows, CT columns); grid.x over column groups.
+template <int L, bool LOWER, bool UNIT, bool CONJT>
+__global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int CT = blockDim.y;
+  const int64_t c = (int64_t)blockIdx.x * CT + ty;
+  const bool ok = tx < bs && c < ncols;
+  extern __shared__ double s_x[];  // [CT][2L]
+  Z<L> x;
+  if (ok) x = ldz<L>(X, k0 + tx, c);
+  for (int s = 0; s < bs; s++) {
+    const int k = LOWER ? s : bs - 1 - s;
+    if (ok && tx == k) {
+      if (!UNIT) {
+        Z<L> d = ldz<L>(A, k0 + k, k0 + k);
+        if (CONJT) d = z_conj<L>(d);
+        x = z_div<L>(x, d);
+      }
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        s_x[ty * 2 * L + q] = x.re.x[q];
+        s_x[ty * 2 * L + L + q] = x.im.x[q];
+      }
+    }
+    __syncthreads();
+    if (ok && (LOWER ? tx > k : tx < k)) {
+      Z<L> t = CONJT ? z_conj<L>(ldz<L>(A, k0 + k, k0 + tx)) : ldz<L>(A, k0 + tx, k0 + k);
+      Z<L> xk;
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        xk.re.x[q] = s_x[ty * 2 * L + q];
+        xk.im.x[q] = s_x[ty * 2 * L + L + q];
+      }
+      x = z_fms<L>(x, t, xk);
+    }
+    __syncthreads();
+  }
+  if (ok) stz<L>(X, k0 + tx, c, x);
+}
+
+// X[r, c] -= sum_{k < bs} T(r, k0+k) X[k0+k, c] for rows r in [r0, r1), where
+// T(r, k) = A(r, k), or conj(A(k, r)) with CONJT.  One thread per (row, column)
+// accumulates the bs products on the leveled accumulator (one renormalisation
+// per output).  The A tile and the X block are staged through shared memory
+// 16 k at a time; with CONJT the A tile is read along its columns, which are
+// contiguous in memory, and transposed in shared memory.
+template <int L, bool CONJT>
+__global__ void __launch_bounds__(256) k_gemv(View A, int64_t r0, int64_t r1, int64_t k0, int bs, View X,
+                                              int64_t ncols) {
+  constexpr int TR = 32, TCC = 8, KC = 16;
+  __shared__ double sA[KC][TR][2 * L];
+  __shared__ double sX[KC][TCC][2 * L];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // (32, 8)
+  const int tid = ty * TR + tx;
+  const int64_t r = r0 + (int64_t)blockIdx.x * TR + tx;
+  const int64_t c = (int64_t)blockIdx.y * TCC + ty;
+  Acc<L> are, aim;
+  const bool ok = r < r1 && c < ncols;
+  if (ok) {
+    Z<L> x0 = ldz<L>(X, r, c);
+    are.set(x0.re);
+    aim.set(x0.im);
+  }
+  for (int kk = 0; kk < bs; kk += KC) {
+    // stage A tile: KC x TR elements
+    for (int t = tid; t < KC * TR; t += 256) {
+      int kq, rq;
+      if (CONJT) {  // consecutive threads walk k (contiguous in column r of A)
+        kq = t % KC;
+        rq = t / KC;
+      } else {      // consecutive threads walk r (contiguous in column k of A)
+        rq = t % TR;
+        kq = t / TR;
+      }
+      const int64_t gr = r0 + (int64_t)blockIdx.x * TR + rq, gk = k0 + kk + kq;
+      Z<L> v = z_zero<L>();
+      if (gr < r1 && kk + kq < bs) v = CONJT ? z_conj<L>(ldz<L>(A, gk, gr)) : ldz<L>(A, gr, gk);
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        sA[kq][rq][q] = v.re.x[q];
+        sA[kq][rq][L + q] = v.im.x[q];
+      }
+    }
+    for (int t = tid; t < KC * TCC; t += 256) {
+      const int kq = t % KC, cq = t / KC;
+      const int64_t gc = (int64_t)blockIdx.y * TCC + cq;
+      Z<L> v = z_zero<L>();
+      if (gc < ncols && kk + kq < bs) v = ldz<L>(X, k0 + kk + kq, gc);
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        sX[kq][cq][q] = v.re.x[q];
+        sX[kq][cq][L + q] = v.im.x[q];
+      }
+    }
+    __syncthreads();
+    if (ok) {
+      const int kmax = min(KC, bs - kk);
+      for (int kq = 0; kq < kmax; kq++) {
+        R<L> ar, ai, xr, xi;
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          ar.x[q] = sA[kq][tx][q];
+          ai.x[q] = sA[kq][tx][L + q];
+          xr.x[q] = sX[kq][ty][q];
+          xi.x[q] = sX[kq][ty][L + q];
+        }
+        are.template add_prod<true>(ar, xr);
+        are.template add_prod<false>(ai, xi);
+        aim.template add_prod<true>(ar, xi);
+        aim.template add_prod<true>(ai, xr);
+      }
+    }
+    __syncthreads();
+  }
+  if (ok) {
+    Z<L> z;
+    z.re = are.result();
+    z.im = aim.result();
+    stz<L>(X, r, c, z);
+  }
+}
+
+// Plain complex multi-component GEMM on the FP64 pipe: C (m x n) = C - A B
+// (BETA) or A B.  4M (Eq. 1): Re and Im accumulated directly.  3M (Eq. 3):
+// T1 = ReA ReB, T2 = ImA ImB, T3 = (ReA+ImA)(ReB+ImB) accumulated separately,
+// then Re = T1 - T2, Im = T3 - (T1 + T2); SA, SB hold the precomputed sums.
+// One thread per output, k ascending (deterministic), 16 x 16 tile, k staged
+// through shared memory 16 at a time.
+template <int L, bool M3, bool BETA>
+__global__ void __launch_bounds__(GEMM_T *GEMM_T)
+    k_gemm(View A, View B, View C, View SA, View SB, int64_t m, int64_t n, int64_t k) {
+  constexpr int T = GEMM_T;
+  constexpr int NP = M3 ? 3 * L : 2 * L;  // planes staged per operand
+  __shared__ double sA[T][T][NP];         // [k][row][plane]
+  __shared__ double sB[T][T][NP];         // [k][col][plane]
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * T + tx;
+  const int64_t i0 = (int64_t)blockIdx.x * T, j0 = (int64_t)blockIdx.y * T;
+  const int64_t i = i0 + tx, j = j0 + ty;
+  const bool ok = i < m && j < n;
+  Acc<L> a1, a2, a3;
+  a1.zero();
+  a2.zero();
+  a3.zero();
+  for (int64_t kk = 0; kk < k; kk += T) {
+    {  // A tile: thread (tx, ty) loads A[i0+tx, kk+ty]
+      const int64_t gi = i0 + tx, gk = kk + ty;
+      const bool in = gi < m && gk < k;
+#pragma unroll
+      for (int pl = 0; pl < 2 * L; pl++) sA[ty][tx][pl] = in ? A.p[(int64_t)pl * A.ps + gk * A.ld + gi] : 0.0;
+      if constexpr (M3) {
+#pragma unroll
+        for (int q = 0; q < L; q++) sA[ty][tx][2 * L + q] = in ? SA.p[(int64_t)q * SA.ps + gk * SA.ld + gi] : 0.0;
+      }
+    }
+    {  // B tile: thread (tx, ty) loads B[kk+tx, j0+ty]
+      const int64_t gk = kk + tx, gj = j0 + ty;
+      const bool in = gk < k && gj < n;
+#pragma unroll
+      for (int pl = 0; pl < 2 * L; pl++) sB[tx][ty][pl] = in ? B.p[(int64_t)pl * B.ps + gj * B.ld + gk] : 0.0;
+      if constexpr (M3) {
+#pragma unroll
+        for (int q = 0; q < L; q++) sB[tx][ty][2 * L + q] = in ? SB.p[(int64_t)q * SB.ps + gj * SB.ld + gk] : 0.0;
+      }
+    }
+    __syncthreads();
+    const int kmax = (int)min((int64_t)T, k - kk);
+    for (int kq = 0; kq < kmax; kq++) {
+      R<L> ar, ai, br, bi;
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        ar.x[q] = sA[kq][tx][q];
+        ai.x[q] = sA[kq][tx][L + q];
+        br.x[q] = sB[kq][ty][q];
+        bi.x[q] = sB[kq][ty][L + q];
+      }
+      if constexpr (!M3) {
+        // a1 = Re, a2 = Im; BETA subtracts the product
+        a1.template add_prod<BETA>(ar, br);
+        a1.template add_prod<!BETA>(ai, bi);
+        a2.template add_prod<BETA>(ar, bi);
+        a2.template add_prod<BETA>(ai, br);
+      } else {
+        R<L> sa, sb;
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          sa.x[q] = sA[kq][tx][2 * L + q];
+          sb.x[q] = sB[kq][ty][2 * L + q];
+        }
+        a1.template add_prod<false>(ar, br);
+        a2.template add_prod<false>(ai, bi);
+        a3.template add_prod<false>(sa, sb);
+      }
+    }
+    __syncthreads();
+  }
+  (void)tid;
+  if (!ok) return;
+  Z<L> out;
+  if constexpr (!M3) {
+    if (BETA) {
+      Z<L> c0 = ldz<L>(C, i, j);
+      a1.add(c0.re);
+      a2.add(c0.im);
+    }
+    out.re = a1.result();
+    out.im = a2.result();
+  } else {
+    // Re = [C] - T1 + T2 (BETA) or T1 - T2;  Im = [C] - T3 + T1 + T2 or T3 - (T1 + T2)
+    Acc<L> re, im;
+    if (BETA) {
+      Z<L> c0 = ldz<L>(C, i, j);
+      re.set(c0.re);
+      im.set(c0.im);
+    } else {
+      re.zero();
+      im.zero();
+    }
+    re.add_acc(a1, BETA);
+    re.add_acc(a2, !BETA);
+    im.add_acc(a3, BETA);
+    im.add_acc(a1, !BETA);
+    im.add_acc(a2, !BETA);
+    out.re = re.result();
+    out.im = im.result();
+  }
+  stz<L>(C, i, j, out);
+}
+
+// S = Re + Im for an m x k block (3M pre-sums of Eq. 3), L planes out.
+template <int L>
+__global__ void k_resum(View X, View S, int64_t m, int64_t k) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * k) return;
+  const int64_t i = t % m, j = t / m;
+  Z<L> z = ldz<L>(X, i, j);
+  R<L> s = r_add<L>(z.re, z.im);
+#pragma unroll
+  for (int q = 0; q < L; q++) S.p[(int64_t)q * S.ps + j * S.ld + i] = s.x[q];
+}
+
+// Net permutation of a pivot sequence: perm[i] = source row of row i of P b.
+// One thread in shared memory (n <= max_smem/4), else in global memory.
+static __global__ void k_perm_build(const int32_t *ipiv, int64_t n, int32_t *perm, int use_smem) {
+  extern __shared__ int32_t s_perm[];
+  if (threadIdx.x != 0) return;
+  int32_t *P = use_smem ? s_perm : perm;
+  for (int64_t i = 0; i < n; i++) P[i] = (int32_t)i;
+  for (int64_t k = 0; k < n; k++) {
+    int64_t p = ipiv[k] - 1;
+    int32_t a = P[k];
+    P[k] = P[p];
+    P[p] = a;
+  }
+  if (use_smem)
+    for (int64_t i = 0; i < n; i++) perm[i] = P[i];
+}
+
+// Y[i] = X[perm[i]] (gather) or Y[perm[i]] = X[i] (scatter), all 2L planes.
+template <int L>
+__global__ void k_permute(View X, View Y, const int32_t *perm, int64_t n, int64_t ncols, int scatter) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ncols) return;
+  const int64_t i = t % n, c = t / n;
+  const int64_t s = perm[i];
+#pragma unroll
+  for (int pl = 0; pl < 2 * L; pl++) {
+    if (scatter)
+      Y.p[(int64_t)pl * Y.ps + c * Y.ld + s] = X.p[(int64_t)pl * X.ps + c * X.ld + i];
+    else
+      Y.p[(int64_t)pl * Y.ps + c * Y.ld + i] = X.p[(int64_t)pl * X.ps + c * X.ld + s];
+  }
+}
+
+// Abar[i, j] = -lambda_i conj(x_j)
+template <int L>
+__global__ void k_rank1_adjoint(View lam, View x, View Ab, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= n) return;
+  Z<L> l = ldz<L>(lam, i, 0);
+  Z<L> xj = z_conj<L>(ldz<L>(x, j, 0));
+  stz<L>(Ab, i, j, z_neg<L>(z_mul<L>(l, xj)));
+}
+
+// Elementwise operations (mclu_vec_op).
+template <int L>
+__global__ void k_vec_op(int op, int64_t count, const double *x, const double *y, double *z) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  if (op < 10) {
+    R<L> a, b;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      a.x[q] = x[q * count + e];
+      b.x[q] = y[q * count + e];
+    }
+    R<L> r;
+    switch (op) {
+      case 0: r = r_add<L>(a, b); break;
+      case 1: r = r_sub<L>(a, b); break;
+      case 2: r = r_mul<L>(a, b); break;
+      default: r = r_div<L>(a, b); break;
+    }
+#pragma unroll
+    for (int q = 0; q < L; q++) z[q * count + e] = r.x[q];
+    return;
+  }
+  View vx{const_cast<double *>(x), count, count};
+  View vy{const_cast<double *>(y), count, count};
+  View vz{z, count, count};
+  Z<L> a = ldz<L>(vx, e, 0), b, r;
+  if (op != 15 && op != 16) b = ldz<L>(vy, e, 0);
+  switch (op) {
+    case 10: r = z_add<L>(a, b); break;
+    case 11: r = z_sub<L>(a, b); break;
+    case 12: r = z_mul<L>(a, b); break;
+    case 13: r = z_mul3m<L>(a, b); break;
+    case 14: r = z_div<L>(a, b); break;
+    case 15: r = z_inv<L>(a); break;
+    default:
+      r.re = z_abs1<L>(a);
+      r.im = r_zero<L>();
+      break;
+  }
+  stz<L>(vz, e, 0, r);
+}
+
+}  // namespace mclu

@@ -1,0 +1,554 @@
+// mc.cuh - device library of error-free transformations and multi-component
+// (DD / TD / QD, L = 2 / 3 / 4 binary64 limbs) real and complex arithmetic.
+//
+// The paper (Sec. 1, Sec. 2.2) builds its complex DD/TD/QD operations on
+// multi-component real arithmetic without printing the algorithms.  This file
+// implements them from the published building blocks:
+//   * TwoSum (Knuth): s = RN(a+b), e = a+b-s exactly, 6 flops, any a, b;
+//   * TwoProd with FMA: p = RN(ab), e = fma(a,b,-p) = ab-p exactly, 2 flops;
+//   * a leveled accumulator: level k collects terms of order u^k (u = 2^-53)
+//     exactly with TwoSum and passes each rounding error down to level k+1;
+//     only the last level (order u^(L-1)) is summed with plain rounding.
+//     Products keep the limb pairs (i, j) with i + j <= L-1 (TwoProd for
+//     i + j <= L-2, a plain FMA into the last level for i + j = L-1); the
+//     dropped pairs are below u^L relative.  This is the compensated-dot idea
+//     of Ogita, Rump and Oishi (Dot2) carried to L levels;
+//   * renormalisation: a bottom-up TwoSum pass (VecSum) followed by a
+//     top-down TwoSum pass; both are error-free, so the value of the
+//     accumulator is kept exactly while it is put back into nonoverlapping
+//     limbs.
+// Every floating-point operation is written with the _rn intrinsics, so the
+// compiler can neither contract nor reassociate them (the library is also
+// built with -fmad=false).  Divisions call CUDA's correctly rounded __ddiv_rn.
+#pragma once
+
+#include <cstdint>
+
+namespace mclu {
+
+// ------------------------------------------------------------------ EFTs --
+
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+  double x = __dadd_rn(a, b);
+  double bv = __dsub_rn(x, a);
+  double av = __dsub_rn(x, bv);
+  double br = __dsub_rn(b, bv);
+  double ar = __dsub_rn(a, av);
+  s = x;
+  e = __dadd_rn(ar, br);
+}
+
+__device__ __forceinline__ void two_prod(double a, double b, double &p, double &e) {
+  double x = __dmul_rn(a, b);
+  e = __fma_rn(a, b, -x);
+  p = x;
+}
+
+// Integer views (ALU pipe, not the FP64 pipe).
+__device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool is_neg(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ double flip(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+// Monotone integer key of a double (total order consistent with < for non-NaN).
+__device__ __forceinline__ long long order_key(double x) {
+  long long i = __double_as_longlong(x);
+  return i >= 0 ? i : (i ^ 0x7fffffffffffffffLL);
+}
+
+// ------------------------------------------------------------ MC values --
+
+template <int L>
+struct R {  // real multi-component value: x[0] + ... + x[L-1]
+  double x[L];
+};
+
+template <int L>
+struct Z {  // complex: separate real and imaginary MC parts (Sec. 2.2)
+  R<L> re, im;
+};
+
+template <int L>
+__device__ __forceinline__ R<L> r_zero() {
+  R<L> r;
+#pragma unroll
+  for (int i = 0; i < L; i++) r.x[i] = 0.0;
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ Z<L> z_zero() {
+  Z<L> r;
+  r.re = r_zero<L>();
+  r.im = r_zero<L>();
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ R<L> r_neg(const R<L> &a) {
+  R<L> r;
+#pragma unroll
+  for (int i = 0; i < L; i++) r.x[i] = flip(a.x[i]);
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ R<L> r_abs(const R<L> &a) {
+  return is_neg(a.x[0]) ? r_neg(a) : a;
+}
+
+template <int L>
+__device__ __forceinline__ Z<L> z_conj(const Z<L> &a) {
+  Z<L> r;
+  r.re = a.re;
+  r.im = r_neg(a.im);
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ Z<L> z_neg(const Z<L> &a) {
+  Z<L> r;
+  r.re = r_neg(a.re);
+  r.im = r_neg(a.im);
+  return r;
+}
+
+// Renormalise N doubles in place: bottom-up TwoSum pass, then a top-down
+// TwoSum pass over the remaining pairs.  Exact; leaves nonoverlapping limbs
+// with leading zeros moved out of the way.
+template <int N>
+__device__ __forceinline__ void renorm_n(double *x) {
+  if constexpr (N == 1) {
+    return;
+  } else {
+    double c = x[N - 1];
+#pragma unroll
+    for (int i = N - 2; i >= 0; i--) {
+      double h, l;
+      two_sum(x[i], c, h, l);
+      x[i + 1] = l;
+      c = h;
+    }
+    x[0] = c;
+#pragma unroll
+    for (int i = 1; i < N - 1; i++) {
+      double h, l;
+      two_sum(x[i], x[i + 1], h, l);
+      x[i] = h;
+      x[i + 1] = l;
+    }
+    // A zero limb above a nonzero one can survive both passes only for N >= 4;
+    // shift such limbs up (integer selects, no FP64 work).
+    if constexpr (N >= 4) {
+#pragma unroll
+      for (int p = 0; p < N - 2; p++) {
+#pragma unroll
+        for (int i = 1; i < N - 1; i++) {
+          bool z = is_zero(x[i]);
+          double a = x[i], b = x[i + 1];
+          x[i] = z ? b : a;
+          x[i + 1] = z ? 0.0 : b;
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------ leveled accumulator --
+
+template <int L>
+struct Acc {
+  double s[L];
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < L; i++) s[i] = 0.0;
+  }
+  __device__ __forceinline__ void set(const R<L> &c) {
+#pragma unroll
+    for (int i = 0; i < L; i++) s[i] = c.x[i];
+  }
+
+  // add v (a term of order u^LV) exactly into level LV, errors cascade down
+  template <int LV>
+  __device__ __forceinline__ void dep(double v) {
+    if constexpr (LV >= L - 1) {
+      s[L - 1] = __dadd_rn(s[L - 1], v);
+    } else {
+      double h, e;
+      two_sum(s[LV], v, h, e);
+      s[LV] = h;
+      dep<LV + 1>(e);
+    }
+  }
+
+  // s += a * b (NEG: s -= a * b; the sign is folded into the multiplies)
+  template <bool NEG = false>
+  __device__ __forceinline__ void add_prod(const R<L> &A, const R<L> &B) {
+    const double *b = B.x;
+    double a[L];
+#pragma unroll
+    for (int q = 0; q < L; q++) a[q] = NEG ? -A.x[q] : A.x[q];
+    if constexpr (L == 2) {
+      double p, e;
+      two_prod(a[0], b[0], p, e);
+      dep<0>(p);
+      s[1] = __dadd_rn(s[1], e);
+      s[1] = __fma_rn(a[0], b[1], s[1]);
+      s[1] = __fma_rn(a[1], b[0], s[1]);
+    } else if constexpr (L == 3) {
+      double p00, e00, p01, e01, p10, e10;
+      two_prod(a[0], b[0], p00, e00);
+      two_prod(a[0], b[1], p01, e01);
+      two_prod(a[1], b[0], p10, e10);
+      dep<0>(p00);
+      dep<1>(e00);
+      dep<1>(p01);
+      dep<1>(p10);
+      s[2] = __dadd_rn(s[2], e01);
+      s[2] = __dadd_rn(s[2], e10);
+      s[2] = __fma_rn(a[0], b[2], s[2]);
+      s[2] = __fma_rn(a[1], b[1], s[2]);
+      s[2] = __fma_rn(a[2], b[0], s[2]);
+    } else {
+      static_assert(L == 4, "L must be 2, 3 or 4");
+      double p00, e00, p01, e01, p10, e10, p02, e02, p11, e11, p20, e20;
+      two_prod(a[0], b[0], p00, e00);
+      two_prod(a[0], b[1], p01, e01);
+      two_prod(a[1], b[0], p10, e10);
+      two_prod(a[0], b[2], p02, e02);
+      two_prod(a[1], b[1], p11, e11);
+      two_prod(a[2], b[0], p20, e20);
+      dep<0>(p00);
+      dep<1>(e00);
+      dep<1>(p01);
+      dep<1>(p10);
+      dep<2>(e01);
+      dep<2>(e10);
+      dep<2>(p02);
+      dep<2>(p11);
+      dep<2>(p20);
+      s[3] = __dadd_rn(s[3], e02);
+      s[3] = __dadd_rn(s[3], e11);
+      s[3] = __dadd_rn(s[3], e20);
+      s[3] = __fma_rn(a[0], b[3], s[3]);
+      s[3] = __fma_rn(a[1], b[2], s[3]);
+      s[3] = __fma_rn(a[2], b[1], s[3]);
+      s[3] = __fma_rn(a[3], b[0], s[3]);
+    }
+  }
+
+  // s = a * b for an empty accumulator (skips the TwoSums against zeros)
+  __device__ __forceinline__ void set_prod(const R<L> &A, const R<L> &B) {
+    const double *a = A.x, *b = B.x;
+    if constexpr (L == 2) {
+      two_prod(a[0], b[0], s[0], s[1]);
+      s[1] = __fma_rn(a[0], b[1], s[1]);
+      s[1] = __fma_rn(a[1], b[0], s[1]);
+    } else if constexpr (L == 3) {
+      double e01, e10, p01, p10;
+      two_prod(a[0], b[0], s[0], s[1]);
+      two_prod(a[0], b[1], p01, e01);
+      two_prod(a[1], b[0], p10, e10);
+      s[2] = e01;
+      dep<1>(p01);
+      dep<1>(p10);
+      s[2] = __dadd_rn(s[2], e10);
+      s[2] = __fma_rn(a[0], b[2], s[2]);
+      s[2] = __fma_rn(a[1], b[1], s[2]);
+      s[2] = __fma_rn(a[2], b[0], s[2]);
+    } else {
+      double p01, e01, p10, e10, p02, e02, p11, e11, p20, e20;
+      two_prod(a[0], b[0], s[0], s[1]);
+      two_prod(a[0], b[1], p01, e01);
+      two_prod(a[1], b[0], p10, e10);
+      two_prod(a[0], b[2], p02, e02);
+      two_prod(a[1], b[1], p11, e11);
+      two_prod(a[2], b[0], p20, e20);
+      s[2] = e01;
+      s[3] = e02;
+      dep<1>(p01);
+      dep<1>(p10);
+      dep<2>(e10);
+      dep<2>(p02);
+      dep<2>(p11);
+      dep<2>(p20);
+      s[3] = __dadd_rn(s[3], e11);
+      s[3] = __dadd_rn(s[3], e20);
+      s[3] = __fma_rn(a[0], b[3], s[3]);
+      s[3] = __fma_rn(a[1], b[2], s[3]);
+      s[3] = __fma_rn(a[2], b[1], s[3]);
+      s[3] = __fma_rn(a[3], b[0], s[3]);
+    }
+  }
+
+  // s += q * b for a binary64 q
+  __device__ __forceinline__ void add_prod1(double q, const R<L> &B) {
+    const double *b = B.x;
+    double p, e;
+    two_prod(q, b[0], p, e);
+    dep<0>(p);
+    if constexpr (L == 2) {
+      s[1] = __dadd_rn(s[1], e);
+      s[1] = __fma_rn(q, b[1], s[1]);
+    } else if constexpr (L == 3) {
+      double p1, e1;
+      two_prod(q, b[1], p1, e1);
+      dep<1>(e);
+      dep<1>(p1);
+      s[2] = __dadd_rn(s[2], e1);
+      s[2] = __fma_rn(q, b[2], s[2]);
+    } else {
+      double p1, e1, p2, e2;
+      two_prod(q, b[1], p1, e1);
+      two_prod(q, b[2], p2, e2);
+      dep<1>(e);
+      dep<1>(p1);
+      dep<2>(e1);
+      dep<2>(p2);
+      s[3] = __dadd_rn(s[3], e2);
+      s[3] = __fma_rn(q, b[3], s[3]);
+    }
+  }
+
+  // s += c (an L-limb value, limb l deposited at level l)
+  __device__ __forceinline__ void add(const R<L> &c) {
+    dep<0>(c.x[0]);
+    if constexpr (L >= 2) dep<1>(c.x[1]);
+    if constexpr (L >= 3) dep<2>(c.x[2]);
+    if constexpr (L >= 4) dep<3>(c.x[3]);
+  }
+
+  // s += sign * t (another accumulator, level by level)
+  __device__ __forceinline__ void add_acc(const Acc<L> &t, bool negate) {
+    dep<0>(negate ? flip(t.s[0]) : t.s[0]);
+    if constexpr (L >= 2) dep<1>(negate ? flip(t.s[1]) : t.s[1]);
+    if constexpr (L >= 3) dep<2>(negate ? flip(t.s[2]) : t.s[2]);
+    if constexpr (L >= 4) dep<3>(negate ? flip(t.s[3]) : t.s[3]);
+  }
+
+  __device__ __forceinline__ R<L> result() const {
+    R<L> r;
+#pragma unroll
+    for (int i = 0; i < L; i++) r.x[i] = s[i];
+    renorm_n<L>(r.x);
+    return r;
+  }
+};
+
+// ------------------------------------------------------- real operations --
+
+// Accurate addition: every limb of both operands is summed exactly on L
+// levels plus one guard level, then renormalised and rounded to L limbs, so
+// cancellation in the leading limbs keeps relative accuracy.
+template <int L>
+__device__ __forceinline__ R<L> r_add(const R<L> &a, const R<L> &b) {
+  Acc<L + 1> t;
+#pragma unroll
+  for (int i = 0; i < L; i++) t.s[i] = a.x[i];
+  t.s[L] = 0.0;
+  t.template dep<0>(b.x[0]);
+  if constexpr (L >= 2) t.template dep<1>(b.x[1]);
+  if constexpr (L >= 3) t.template dep<2>(b.x[2]);
+  if constexpr (L >= 4) t.template dep<3>(b.x[3]);
+  renorm_n<L + 1>(t.s);
+  R<L> r;
+#pragma unroll
+  for (int i = 0; i < L; i++) r.x[i] = t.s[i];
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ R<L> r_sub(const R<L> &a, const R<L> &b) {
+  return r_add<L>(a, r_neg<L>(b));
+}
+
+template <int L>
+__device__ __forceinline__ R<L> r_mul(const R<L> &a, const R<L> &b) {
+  Acc<L> t;
+  t.set_prod(a, b);
+  return t.result();
+}
+
+// Long division: q_k = RN(r_k[0] / b[0]), r_{k+1} = r_k - q_k b (L levels),
+// L+1 quotient digits renormalised to L limbs.
+template <int L>
+__device__ __forceinline__ R<L> r_div(const R<L> &a, const R<L> &b) {
+  double q[L + 1];
+  R<L> r = a;
+#pragma unroll
+  for (int k = 0; k <= L; k++) {
+    q[k] = __ddiv_rn(r.x[0], b.x[0]);
+    if (k < L) {
+      Acc<L> t;
+      t.set(r);
+      t.add_prod1(flip(q[k]), b);
+      r = t.result();
+    }
+  }
+  renorm_n<L + 1>(q);
+  R<L> z;
+#pragma unroll
+  for (int i = 0; i < L; i++) z.x[i] = q[i];
+  return z;
+}
+
+// Lexicographic comparison of renormalised values (nonoverlapping limbs):
+// returns true if a > b.  Integer compares only.
+template <int L>
+__device__ __forceinline__ bool r_gt(const R<L> &a, const R<L> &b) {
+#pragma unroll
+  for (int i = 0; i < L; i++) {
+    long long ka = order_key(a.x[i]), kb = order_key(b.x[i]);
+    if (ka != kb) return ka > kb;
+  }
+  return false;
+}
+
+// ---------------------------------------------------- complex operations --
+
+template <int L>
+__device__ __forceinline__ Z<L> z_add(const Z<L> &a, const Z<L> &b) {
+  Z<L> r;
+  r.re = r_add<L>(a.re, b.re);
+  r.im = r_add<L>(a.im, b.im);
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ Z<L> z_sub(const Z<L> &a, const Z<L> &b) {
+  Z<L> r;
+  r.re = r_sub<L>(a.re, b.re);
+  r.im = r_sub<L>(a.im, b.im);
+  return r;
+}
+
+// Eq. (1), each part accumulated on the leveled accumulator:
+// Re = Re a Re b - Im a Im b,  Im = Re a Im b + Im a Re b.
+template <int L>
+__device__ __forceinline__ Z<L> z_mul(const Z<L> &a, const Z<L> &b) {
+  Z<L> r;
+  Acc<L> t;
+  t.set_prod(a.re, b.re);
+  t.template add_prod<true>(a.im, b.im);
+  r.re = t.result();
+  t.set_prod(a.re, b.im);
+  t.add_prod(a.im, b.re);
+  r.im = t.result();
+  return r;
+}
+
+// Eq. (2): t1 = Re a Re b, t2 = Im a Im b, Re = t1 - t2,
+// Im = (Re a + Im a)(Re b + Im b) - (t1 + t2), every step rounded to L limbs.
+template <int L>
+__device__ __forceinline__ Z<L> z_mul3m(const Z<L> &a, const Z<L> &b) {
+  R<L> t1 = r_mul<L>(a.re, b.re);
+  R<L> t2 = r_mul<L>(a.im, b.im);
+  R<L> t3 = r_mul<L>(r_add<L>(a.re, a.im), r_add<L>(b.re, b.im));
+  Z<L> r;
+  r.re = r_sub<L>(t1, t2);
+  r.im = r_sub<L>(t3, r_add<L>(t1, t2));
+  return r;
+}
+
+// |a|^2 = Re a^2 + Im a^2
+template <int L>
+__device__ __forceinline__ R<L> z_norm2(const Z<L> &a) {
+  Acc<L> t;
+  t.set_prod(a.re, a.re);
+  t.add_prod(a.im, a.im);
+  return t.result();
+}
+
+// 1/(a + bi) = (a - bi) / (a^2 + b^2)
+template <int L>
+__device__ __forceinline__ Z<L> z_inv(const Z<L> &a) {
+  R<L> one = r_zero<L>();
+  one.x[0] = 1.0;
+  R<L> rinv = r_div<L>(one, z_norm2<L>(a));
+  Z<L> r;
+  r.re = r_mul<L>(a.re, rinv);
+  r.im = r_neg<L>(r_mul<L>(a.im, rinv));
+  return r;
+}
+
+// a / b = a conj(b) / |b|^2 with both real parts divided by long division
+template <int L>
+__device__ __forceinline__ Z<L> z_div(const Z<L> &a, const Z<L> &b) {
+  Z<L> num = z_mul<L>(a, z_conj<L>(b));
+  R<L> d = z_norm2<L>(b);
+  Z<L> r;
+  r.re = r_div<L>(num.re, d);
+  r.im = r_div<L>(num.im, d);
+  return r;
+}
+
+// cabs1(z) = |Re z| + |Im z| (the pivot key; LAPACK's izamax measure)
+template <int L>
+__device__ __forceinline__ R<L> z_abs1(const Z<L> &a) {
+  return r_add<L>(r_abs<L>(a.re), r_abs<L>(a.im));
+}
+
+// Pivot key: cabs1 with its two leading limbs made a TwoSum pair, so that
+// limb 0 is the rounded value of limbs 0 + 1 and the lexicographic comparison
+// of r_gt orders keys by value (exactly for DD; for TD/QD up to ties in the
+// third limb).
+template <int L>
+__device__ __forceinline__ R<L> pivot_key(const Z<L> &a) {
+  R<L> k = z_abs1<L>(a);
+  double h, l;
+  two_sum(k.x[0], k.x[1], h, l);
+  k.x[0] = h;
+  k.x[1] = l;
+  return k;
+}
+
+// c - a b on the leveled accumulator (one renormalisation per part)
+template <int L>
+__device__ __forceinline__ Z<L> z_fms(const Z<L> &c, const Z<L> &a, const Z<L> &b) {
+  Z<L> r;
+  Acc<L> t;
+  t.set(c.re);
+  t.template add_prod<true>(a.re, b.re);
+  t.template add_prod<false>(a.im, b.im);
+  r.re = t.result();
+  t.set(c.im);
+  t.template add_prod<true>(a.re, b.im);
+  t.template add_prod<true>(a.im, b.re);
+  r.im = t.result();
+  return r;
+}
+
+// ---------------------------------------------------------- plane access --
+
+// A complex L-limb matrix: 2L column-major planes, plane (c,l) at
+// p + (c*L + l)*ps, element (i,j) at offset j*ld + i.
+struct View {
+  double *p;
+  int64_t ld;
+  int64_t ps;
+};
+
+template <int L>
+__device__ __forceinline__ Z<L> ldz(const View &v, int64_t i, int64_t j) {
+  Z<L> z;
+  const int64_t o = j * v.ld + i;
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    z.re.x[l] = v.p[(int64_t)l * v.ps + o];
+    z.im.x[l] = v.p[(int64_t)(L + l) * v.ps + o];
+  }
+  return z;
+}
+
+template <int L>
+__device__ __forceinline__ void stz(const View &v, int64_t i, int64_t j, const Z<L> &z) {
+  const int64_t o = j * v.ld + i;
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    v.p[(int64_t)l * v.ps + o] = z.re.x[l];
+    v.p[(int64_t)(L + l) * v.ps + o] = z.im.x[l];
+  }
+}
+
+}  // namespace mclu

@@ -30,14 +30,15 @@ def frac_vec(x: np.ndarray) -> list[Fraction]:
     return [frac_col(x, j) for j in range(x.shape[1])]
 
 
-def is_nonoverlapping(limbs) -> bool:
-    """|x_{k+1}| <= ulp(x_k)/2 for every adjacent nonzero pair and zeros only at the end."""
+def is_nonoverlapping(limbs, strict: bool = True) -> bool:
+    """|x_{k+1}| <= ulp(x_k)/2 (strict) or <= ulp(x_k) (ulp-nonoverlapping) for every
+    adjacent nonzero pair, and zeros only at the end."""
     seen_zero = False
     for a, b in zip(limbs[:-1], limbs[1:]):
         if a == 0:
             seen_zero = True
         if seen_zero and b != 0:
             return False
-        if a != 0 and abs(b) > np.spacing(abs(a)) / 2:
+        if a != 0 and abs(b) > np.spacing(abs(a)) / (2 if strict else 1):
             return False
     return True

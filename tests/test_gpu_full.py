@@ -1,0 +1,67 @@
+"""Full-size checks at n = 4096 in the benchmark's launch configuration
+(blocked, nb = 64, 4M and 3M trailing update), by properties that hold at any
+size and that the oracle can evaluate one output at a time:
+
+* backward error with the exact residual: ||b - A x|| / (||A|| ||x||) <= 16 n u;
+* sampled entries of L U equal those of P A within 2^6 n u max|A|
+  (each entry is an exact dot product evaluated by the oracle);
+* partial pivoting on cabs1 bounds every multiplier: |l_ik| <= sqrt(2).
+"""
+import numpy as np
+import pytest
+
+from gpu_util import backward_error, bound, dev, host
+from helpers import U_EXP
+from paper_2403_16013_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_16013_gb300 import api as a
+    from paper_2403_16013_gb300 import build
+    build.build()
+    return a
+
+
+def _apply_pivots(A, ipiv):
+    P = np.arange(A.shape[3])
+    for k, p in enumerate(ipiv - 1):
+        P[k], P[p] = P[p], P[k]
+    return P
+
+
+@pytest.mark.parametrize("prec,method", [("dd", "4m"), ("dd", "3m"), ("td", "4m"), ("qd", "4m")])
+def test_full_size(api, orc, prec, method):
+    import torch
+    L = {"dd": 2, "td": 3, "qd": 4}[prec]
+    n = 4096
+    A = inputs.gaussian_matrix(n, L, seed=1)
+    b = inputs.complex_gaussian_vector(n, L, seed=2)
+    Ad = dev(A)
+    LU, ipiv, info = api.lu_factor(Ad, method=method, nb=64)
+    x = api.lu_solve(LU, ipiv, dev(b))
+    torch.cuda.synchronize()
+    assert int(host(info)[0]) == 0
+    X, LUh, ip = host(x), host(LU), host(ipiv)
+    del Ad, LU, x
+    eta = backward_error(orc, A, X, b)
+    assert eta <= bound(n, L), eta
+    # multipliers bounded by sqrt(2)
+    Lval = np.hypot(LUh[0, 0], LUh[1, 0])            # [col, row] magnitudes of the leading limbs
+    low = np.tril(np.ones((n, n), bool), -1).T       # (col, row) with row > col
+    assert Lval[low].max() <= np.sqrt(2) * (1 + 1e-12)
+    # sampled entries of L U against P A
+    rng = np.random.default_rng(9)
+    rows = rng.integers(0, n, 96)
+    cols = rng.integers(0, n, 96)
+    P = _apply_pivots(A, ip)
+    PA = np.ascontiguousarray(A[:, :, :, P])
+    d = orc.exact_entries(LUh, LUh, rows, cols, C=PA, sign=-1, lu=True)   # exact P A - L U, rounded
+    amax = np.abs(A[:, 0]).max()
+    err = np.abs(d[:, :, 0]).max()
+    assert err <= 2.0 ** 6 * n * 2.0 ** -U_EXP[L] * amax, err
