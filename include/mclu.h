@@ -37,6 +37,7 @@ extern "C" {
 #endif
 
 #define MCLU_ERR_UNSUPPORTED 100000
+#define MCLU_ERR_SCRATCH_CAPACITY 100001
 
 /* Trailing-update methods (Sec. 2.1 and Sec. 3). */
 enum {
@@ -85,6 +86,26 @@ int zgetrf_td_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info
                  void *stream);
 int zgetrf_qd_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
                  void *stream);
+
+/*
+ * zgetrf_dd_noalloc: zgetrf_dd_ex with the defaults (4M, nb = 64) that
+ * allocates no memory.  The paper has no counterpart: this serves callers
+ * that may not allocate device memory during the call (inside a CUDA graph
+ * capture, real-time code that allows no allocator calls after start-up, or
+ * a host that gives the library only its own buffers).  Its scratch is one
+ * fixed device array in the library (about 540 KB, held on every GPU that
+ * loads the library until the process exits), so:
+ *   n     0 <= n <= zgetrf_dd_noalloc_max_n() (8192); larger n returns
+ *         MCLU_ERR_SCRATCH_CAPACITY and enqueues nothing
+ *   A, lda, ipiv, info, stream  as in zgetrf_dd_ex (info may be NULL)
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it: make that first call before any stream
+ * capture.  All calls share the array: calls that can overlap on the GPU
+ * (several streams or host threads) race and must be serialised by the
+ * caller.  Counters that must start at zero are cleared by every call.
+ */
+int zgetrf_dd_noalloc(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, void *stream);
+int64_t zgetrf_dd_noalloc_max_n(void);
 
 /*
  * zgetrs_{dd,td,qd}: solve with the factors of zgetrf (Sec. 4: "forward and

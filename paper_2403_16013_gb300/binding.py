@@ -39,6 +39,8 @@ def _declare(lib):
         f = getattr(lib, f"zadjoint_rank1_{s}")
         f.argtypes, f.restype = [i64, vp, vp, vp, i64, vp], ci
     lib.mclu_vec_op.argtypes, lib.mclu_vec_op.restype = [ci, ci, i64, vp, vp, vp, vp], ci
+    lib.zgetrf_dd_noalloc.argtypes, lib.zgetrf_dd_noalloc.restype = [i64, vp, i64, vp, vp, vp], ci
+    lib.zgetrf_dd_noalloc_max_n.argtypes, lib.zgetrf_dd_noalloc_max_n.restype = [], i64
     lib.mclu_status_string.argtypes, lib.mclu_status_string.restype = [ci], C.c_char_p
     lib.mclu_version.argtypes, lib.mclu_version.restype = [], C.c_char_p
     lib.mclu_launch_count.argtypes, lib.mclu_launch_count.restype = [], C.c_uint64
@@ -105,6 +107,10 @@ def zgetrf(prec: str, n, A, lda, ipiv, stream=None) -> int:
 def zgetrf_ex(prec: str, n, A, lda, ipiv, info, nb=0, method=METHOD_4M, ozaki_slices=0, stream=None) -> int:
     o = MCLUOpts(nb, method, ozaki_slices, 0)
     return getattr(load(), f"zgetrf_{prec}_ex")(n, A, lda, ipiv, info, C.byref(o), _stream(stream))
+
+
+def zgetrf_dd_noalloc(n, A, lda, ipiv, info, stream=None) -> int:
+    return load().zgetrf_dd_noalloc(n, A, lda, ipiv, info, _stream(stream))
 
 
 def zgetrs(prec: str, trans: str, n, nrhs, A, lda, ipiv, B, ldb, stream=None) -> int:

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmclu.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["mclu_common.cu", "mclu_dd.cu", "mclu_td.cu", "mclu_qd.cu"]
+SOURCES = ["mclu_common.cu", "mclu_dd.cu", "mclu_td.cu", "mclu_qd.cu", "mclu_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

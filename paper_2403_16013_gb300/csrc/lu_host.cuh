@@ -28,7 +28,7 @@ void note_launch();
     MCLU_TRY(cudaGetLastError());  \
   } while (0)
 
-inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+constexpr int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Launch classes timed by mclu_profile_begin / mclu_profile_end.
 enum ProfKind { PK_PANEL = 0, PK_LASWP = 1, PK_TRSM = 2, PK_GEMM = 3, PK_SOLVE = 4, PK_OTHER = 5, PK_COUNT = 6 };
@@ -82,8 +82,8 @@ struct Carver {  // 256-byte aligned sub-allocations of one workspace block
 };
 
 template <int L>
-size_t getrf_ws_bytes(int64_t n, int nb, bool m3) {
-  size_t nparts = (size_t)cdiv(std::max<int64_t>(n, 1), PANEL_T) + 1;
+constexpr size_t getrf_ws_bytes(int64_t n, int nb, bool m3) {
+  size_t nparts = (size_t)(((n > 1 ? n : 1) + PANEL_T - 1) / PANEL_T) + 1;
   size_t b = 4 * 256;                                           // counter, info, zflag, recip
   b += ((nparts * L * sizeof(double)) + 255) & ~(size_t)255;   // part_key
   b += ((nparts * sizeof(int)) + 255) & ~(size_t)255;          // part_idx
@@ -124,9 +124,11 @@ int launch_resum(View X, View S, int64_t m, int64_t k, cudaStream_t s) {
 // Right-looking blocked LU (Sec. 3): for each panel of width nb: factor the
 // panel (pivot search, swap, scale, rank-1 steps), swap the rows left and
 // right of it, TRSM for U12, and the trailing update A22 <- A22 - L21 U12.
+// ext_ws / ext_bytes: caller-provided workspace (no allocation in this call);
+// nullptr = allocate stream-ordered workspace.
 template <int L>
 int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
-          cudaStream_t s) {
+          cudaStream_t s, void *ext_ws = nullptr, size_t ext_bytes = 0) {
   if (n < 0) return -1;
   if (n > 0 && Ap == nullptr) return -2;
   if (lda < std::max<int64_t>(1, n)) return -3;
@@ -148,8 +150,16 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   if (method == MCLU_METHOD_UNBLOCKED) nb = (int)std::min<int64_t>(n, INT32_MAX);
   const bool m3 = method == MCLU_METHOD_3M;
   Workspace w;
-  MCLU_TRY(w.alloc(getrf_ws_bytes<L>(n, m3 ? nb : 0, m3), s));
-  Carver cv{(char *)w.p};
+  const size_t ws_need = getrf_ws_bytes<L>(n, m3 ? nb : 0, m3);
+  char *ws_base = nullptr;
+  if (ext_ws) {
+    if (ext_bytes < ws_need) return MCLU_ERR_SCRATCH_CAPACITY;
+    ws_base = (char *)ext_ws;
+  } else {
+    MCLU_TRY(w.alloc(ws_need, s));
+    ws_base = (char *)w.p;
+  }
+  Carver cv{ws_base};
   PanelWS<L> ws;
   char *hdr = cv.take<char>(4 * 256);
   ws.counter = (int *)hdr;

@@ -81,6 +81,7 @@ extern "C" int mclu_vec_op(int op, int L, int64_t count, const double *x, const 
 extern "C" const char *mclu_status_string(int status) {
   if (status == 0) return "ok";
   if (status == MCLU_ERR_UNSUPPORTED) return "request not supported by this build";
+  if (status == MCLU_ERR_SCRATCH_CAPACITY) return "problem too large for the fixed scratch capacity of this entry point";
   if (status < 0) return "invalid argument (status = -index of the argument)";
   return cudaGetErrorString((cudaError_t)status);
 }

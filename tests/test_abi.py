@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "mclu.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(?:int|uint64_t|const char \*)\s*\*?\s*(\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(?:int|int64_t|uint64_t|const char \*)\s*\*?\s*(\w+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
