@@ -42,6 +42,17 @@ LIMBS = {"dd": 2, "td": 3, "qd": 4}
 # FP64 peak: 1.25 TFLOP/s nominal on GB300 counting an FMA as 2 flops, i.e.
 # 0.625e12 FP64 operations per second (2 per clock per SM at 2.07 GHz).
 FP64_OPS_PEAK = 0.625e12
+# Ozaki-scheme engine: slices S per precision; kept pairs p + q <= S - 1.
+OZAKI_S = {"dd": 14, "td": 24, "qd": 32}
+
+
+def measured_bf16_peak() -> tuple[float, str]:
+    """Dense bf16 TFLOP/s from MEASURED_PEAKS.json (burst), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
 
 
 def parse():
@@ -53,7 +64,7 @@ def parse():
     p.add_argument("--prec", default="dd", choices=["dd", "td", "qd"])
     p.add_argument("--method", default="4m", choices=["4m", "3m", "unblocked", "ozaki"])
     p.add_argument("--n", type=int, default=4096)
-    p.add_argument("--nb", type=int, default=64)
+    p.add_argument("--nb", type=int, default=0, help="panel width (0: 64, or 32 for ozaki)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle sample")
@@ -212,6 +223,8 @@ def main():
     build.build()
     binding.load()
     n, L, prec = args.n, LIMBS[args.prec], args.prec
+    if args.nb == 0:
+        args.nb = 32 if args.method == "ozaki" else 64
     A_h, b_h = make_inputs(n, L)
     A0 = torch.from_numpy(A_h).cuda()
     b0 = torch.from_numpy(b_h).cuda()
@@ -265,6 +278,23 @@ def main():
     per_mac = (3 if method == "3m" else 4) * I_REAL[prec]
     gemm_ms, gemm_calls = prof["gemm"]
     roof = None
+    if gemm_calls and method == "ozaki":
+        S = OZAKI_S[prec]
+        pairs = S * (S + 1) // 2
+        # realified real GEMM per pair: (m) x (2 n2) x (2 jb), 2 flops per MAC
+        flops = 0
+        for j0 in range(0, n, nb):
+            jb = min(nb, n - j0)
+            n2 = n - j0 - jb
+            flops += pairs * 2.0 * n2 * (2 * n2) * (2 * jb)
+        per_launch = flops / (gemm_calls / args.steps)
+        achieved = per_launch / (gemm_ms / gemm_calls * 1e-3) / 1e12
+        peak, src = measured_bf16_peak()
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": src, "traffic": None,
+                "kernel": f"k_oz_gemm<{L},beta> (+ split kernels, counted in its time)",
+                "flops_per_launch": per_launch, "avg_launch_ms": gemm_ms / gemm_calls,
+                "share_of_step": gemm_ms / el_ms}
     if gemm_calls and method in ("4m", "3m"):
         per_launch_ops = macs * per_mac / (gemm_calls / args.steps)
         achieved = per_launch_ops / (gemm_ms / gemm_calls * 1e-3)

@@ -45,14 +45,15 @@ enum {
   MCLU_METHOD_3M = 1,        /* 3M matrix product by Eq. (3): T1, T2, T3 then Re = T1 - T2,      */
                              /*   Im = T3 - (T1 + T2)                                              */
   MCLU_METHOD_UNBLOCKED = 2, /* "Normal LU" of Sec. 3: right-looking row elimination, no GEMM    */
-  MCLU_METHOD_OZAKI = 3      /* Ozaki-scheme trailing update (Sec. 2.3): exact slice products    */
+  MCLU_METHOD_OZAKI = 3      /* Ozaki-scheme update (Sec. 2.3): exact bf16 slice products on the */
+                             /*   tensor cores; panel width nb <= 32 (default 32)                 */
 };
 
 /* Optional parameters of the *_ex factorisation calls (NULL = defaults). */
 typedef struct mclu_opts {
   int32_t nb;           /* panel width K of Sec. 3 (block size NDIM); 0 = 64; 1..256          */
   int32_t method;       /* MCLU_METHOD_*; default MCLU_METHOD_4M                             */
-  int32_t ozaki_slices; /* slices per operand for MCLU_METHOD_OZAKI; 0 = precision default     */
+  int32_t ozaki_slices; /* MCLU_METHOD_OZAKI: 0 or the precision's S (14 DD, 24 TD, 32 QD)      */
   int32_t reserved;     /* must be 0                                                          */
 } mclu_opts;
 
@@ -77,7 +78,8 @@ int zgetrf_qd(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream);
 /*
  * zgetrf_{dd,td,qd}_ex: as zgetrf_*, plus
  *   info  device int32[1] or NULL: 0, or k+1 for the first exactly-zero pivot
- *         U[k,k] (LAPACK convention)
+ *         U[k,k] (LAPACK convention); < 0 only if a tensor-core pipeline
+ *         wait of MCLU_METHOD_OZAKI timed out (results invalid)
  *   opts  host pointer or NULL (defaults)
  */
 int zgetrf_dd_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
@@ -149,6 +151,29 @@ int zgemm_qd(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const d
 int zadjoint_rank1_dd(int64_t n, const double *lambda, const double *x, double *Abar, int64_t ldab, void *stream);
 int zadjoint_rank1_td(int64_t n, const double *lambda, const double *x, double *Abar, int64_t ldab, void *stream);
 int zadjoint_rank1_qd(int64_t n, const double *lambda, const double *x, double *Abar, int64_t ldab, void *stream);
+
+/*
+ * zozaki_split_{dd,td,qd}: the slicing step of the Ozaki-scheme product
+ * (Sec. 2.3: split into slices whose products are exact), exposed for
+ * inspection.  X: device rows x cols planes (leading dimension ld).
+ *   side 0 (left operand A, one scale per row): slices = bf16
+ *          [ceil(cols/32)][S][Mpad][64], Mpad = rows rounded up to 128; element
+ *          (i, c) has its real digits at [c/32][p][i][c%32] and imaginary
+ *          digits at [c/32][p][i][32 + c%32]; E int32[rows].
+ *   side 1 (right operand B, one scale per column): slices = bf16
+ *          [ceil(rows/32)][S][Npad][64], Npad = 2 cols rounded up to N
+ *          (N = 32 DD, 16 TD/QD); element (r, j): row 2j holds [Re | -Im] and
+ *          row 2j+1 [Im | Re] at K index r%32 | 32 + r%32; E int32[cols].
+ * Digit p of x is a_p with x ~ 2^E sum_p a_p 2^(-beta (p+1)), beta = 8, 7, 7
+ * and S = 14, 24, 32 for DD, TD, QD.  slices and E are caller-owned device
+ * buffers of those sizes.
+ */
+int zozaki_split_dd(int side, int64_t rows, int64_t cols, const double *X, int64_t ld, void *slices, int32_t *E,
+                    void *stream);
+int zozaki_split_td(int side, int64_t rows, int64_t cols, const double *X, int64_t ld, void *slices, int32_t *E,
+                    void *stream);
+int zozaki_split_qd(int side, int64_t rows, int64_t cols, const double *X, int64_t ld, void *slices, int32_t *E,
+                    void *stream);
 
 /*
  * mclu_vec_op: elementwise multi-component arithmetic on device vectors (the

@@ -38,6 +38,8 @@ def _declare(lib):
         f.argtypes, f.restype = [ci, ci, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp], ci
         f = getattr(lib, f"zadjoint_rank1_{s}")
         f.argtypes, f.restype = [i64, vp, vp, vp, i64, vp], ci
+        f = getattr(lib, f"zozaki_split_{s}")
+        f.argtypes, f.restype = [ci, i64, i64, vp, i64, vp, vp, vp], ci
     lib.mclu_vec_op.argtypes, lib.mclu_vec_op.restype = [ci, ci, i64, vp, vp, vp, vp], ci
     lib.zgetrf_dd_noalloc.argtypes, lib.zgetrf_dd_noalloc.restype = [i64, vp, i64, vp, vp, vp], ci
     lib.zgetrf_dd_noalloc_max_n.argtypes, lib.zgetrf_dd_noalloc_max_n.restype = [], i64
@@ -123,6 +125,10 @@ def zgemm(prec: str, beta_mode, method, m, n, k, A, lda, B, ldb, Cm, ldc, stream
 
 def zadjoint_rank1(prec: str, n, lam, x, Abar, ldab, stream=None) -> int:
     return getattr(load(), f"zadjoint_rank1_{prec}")(n, lam, x, Abar, ldab, _stream(stream))
+
+
+def zozaki_split(prec: str, side, rows, cols, X, ld, slices, E, stream=None) -> int:
+    return getattr(load(), f"zozaki_split_{prec}")(side, rows, cols, X, ld, slices, E, _stream(stream))
 
 
 def vec_op(op, L, count, x, y, z, stream=None) -> int:

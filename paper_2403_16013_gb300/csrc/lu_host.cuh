@@ -11,6 +11,7 @@
 
 #include "../../include/mclu.h"
 #include "lu_kernels.cuh"
+#include "ozaki.cuh"
 
 namespace mclu {
 
@@ -139,8 +140,12 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     if (opts->nb) nb = opts->nb;
     if (opts->method < MCLU_METHOD_4M || opts->method > MCLU_METHOD_OZAKI) return -6;
     method = opts->method;
-    if (method == MCLU_METHOD_OZAKI) return MCLU_ERR_UNSUPPORTED;
     if (opts->reserved != 0) return -6;
+    if (method == MCLU_METHOD_OZAKI) {
+      if (opts->ozaki_slices != 0 && opts->ozaki_slices != oz::Cfg<L>::S) return MCLU_ERR_UNSUPPORTED;
+      if (opts->nb == 0) nb = oz::NB_MAX;
+      if (nb > oz::NB_MAX) return -6;
+    }
   }
   if (n > INT32_MAX - 1) return -1;
   if (n == 0) {
@@ -149,8 +154,10 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   }
   if (method == MCLU_METHOD_UNBLOCKED) nb = (int)std::min<int64_t>(n, INT32_MAX);
   const bool m3 = method == MCLU_METHOD_3M;
+  const bool ozk = method == MCLU_METHOD_OZAKI;
   Workspace w;
-  const size_t ws_need = getrf_ws_bytes<L>(n, m3 ? nb : 0, m3);
+  const size_t oz_need = ozk ? oz::ws_bytes<L>(n, n, nb) : 0;
+  const size_t ws_need = getrf_ws_bytes<L>(n, m3 ? nb : 0, m3) + oz_need;
   char *ws_base = nullptr;
   if (ext_ws) {
     if (ext_bytes < ws_need) return MCLU_ERR_SCRATCH_CAPACITY;
@@ -176,6 +183,8 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     sumL = cv.take<double>((size_t)n * nb * L);
     sumU = cv.take<double>((size_t)n * nb * L);
   }
+  void *oz_ws = ozk ? (void *)cv.take<char>(oz_need) : nullptr;
+  int *oz_status = ws.zflag + 1;  // spare word of the header block
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
   View A{Ap, lda, lda * n};
 
@@ -227,9 +236,14 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
         if (rc) return rc;
       }
       ProfScope ps(PK_GEMM, s);
-      int rc = launch_gemm<L>(method, true, L21, U12, A22, SL, SU, n2, n2, jb, s);
+      int rc = ozk ? oz::gemm<L>(true, L21, U12, A22, n2, n2, jb, oz_ws, oz_status, s, note_launch)
+                   : launch_gemm<L>(method, true, L21, U12, A22, SL, SU, n2, n2, jb, s);
       if (rc) return rc;
     }
+  }
+  if (ozk) {  // a timed-out tensor-core pipeline is reported through info
+    k_merge_status<<<1, 1, 0, s>>>(oz_status, ws.info);
+    MCLU_LAUNCHED();
   }
   if (info) MCLU_TRY(cudaMemcpyAsync(info, ws.info, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   return 0;
@@ -324,10 +338,16 @@ int gemm(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const doubl
   if (m > 0 && n > 0 && Cp == nullptr) return -10;
   if (ldc < std::max<int64_t>(1, m)) return -11;
   if (m == 0 || n == 0) return 0;
-  if (method == MCLU_METHOD_OZAKI) return MCLU_ERR_UNSUPPORTED;
   View A{const_cast<double *>(Ap), lda, lda * k}, B{const_cast<double *>(Bp), ldb, ldb * n}, C{Cp, ldc, ldc * n};
   View SA{nullptr, 0, 0}, SB{nullptr, 0, 0};
   Workspace w;
+  if (method == MCLU_METHOD_OZAKI) {
+    MCLU_TRY(w.alloc(oz::ws_bytes<L>(m, n, k) + 256, s));
+    int *status = (int *)((char *)w.p + oz::ws_bytes<L>(m, n, k));
+    MCLU_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    ProfScope ps(PK_GEMM, s);
+    return oz::gemm<L>(beta_mode == 1, A, B, C, m, n, k, w.p, status, s, note_launch);
+  }
   if (method == MCLU_METHOD_3M && k > 0) {
     MCLU_TRY(w.alloc((size_t)(m * k + k * n) * L * sizeof(double) + 512, s));
     SA = View{(double *)w.p, m, m * k};
@@ -353,6 +373,40 @@ int adjoint_rank1(int64_t n, const double *lam, const double *x, double *Ab, int
   View vl{const_cast<double *>(lam), n, n}, vx{const_cast<double *>(x), n, n}, vA{Ab, ldab, ldab * n};
   k_rank1_adjoint<L><<<dim3((unsigned)cdiv(n, 256), (unsigned)n), 256, 0, s>>>(vl, vx, vA, n);
   MCLU_LAUNCHED();
+  return 0;
+}
+
+// Ozaki split of one operand (diagnostic): side 0 = row-scaled A (rows x cols),
+// side 1 = column-scaled B (rows x cols); slices and exponents copied out.
+template <int L>
+int ozaki_split(int side, int64_t rows, int64_t cols, const double *X, int64_t ld, void *slices, int *E,
+                cudaStream_t s) {
+  if (side != 0 && side != 1) return -2;
+  if (rows < 0) return -3;
+  if (cols < 0) return -4;
+  if (!X && rows > 0 && cols > 0) return -5;
+  if (ld < std::max<int64_t>(1, rows)) return -6;
+  if (!slices) return -7;
+  if (!E) return -8;
+  if (rows == 0 || cols == 0) return 0;
+  View V{const_cast<double *>(X), ld, ld * cols};
+  // reuse the two-operand split with a 1-element dummy on the other side
+  const int64_t m = side == 0 ? rows : 1, n = side == 1 ? cols : 1, k = side == 0 ? cols : rows;
+  const oz::Sizes<L> z = oz::sizes<L>(m, n, k);
+  Workspace w;
+  MCLU_TRY(w.alloc(z.total + 2 * L * 8 * (size_t)(k + 1), s));
+  double *dummy = (double *)((char *)w.p + z.total);
+  MCLU_TRY(cudaMemsetAsync(dummy, 0, 2 * L * 8 * (size_t)(k + 1), s));
+  View D{dummy, side == 0 ? k : 1, side == 0 ? k : k};
+  int rc = side == 0 ? oz::split<L>(V, View{dummy, k, k}, m, n, k, w.p, s, note_launch)
+                     : oz::split<L>(View{dummy, 1, k}, V, m, n, k, w.p, s, note_launch);
+  (void)D;
+  if (rc) return rc;
+  char *base = (char *)w.p;
+  const size_t bytes = side == 0 ? z.a_bytes : z.b_bytes;
+  MCLU_TRY(cudaMemcpyAsync(slices, base + (side == 0 ? 0 : z.a_bytes), bytes, cudaMemcpyDeviceToDevice, s));
+  const int *Es = (const int *)(base + z.a_bytes + z.b_bytes) + (side == 0 ? 0 : z.Mpad);
+  MCLU_TRY(cudaMemcpyAsync(E, Es, (side == 0 ? rows : cols) * sizeof(int), cudaMemcpyDeviceToDevice, s));
   return 0;
 }
 
@@ -396,4 +450,8 @@ int vec_op(int op, int64_t count, const double *x, const double *y, double *z, c
   }                                                                                                              \
   int mclu_vec_op_##SUF(int op, int64_t count, const double *x, const double *y, double *z, void *stream) {     \
     return mclu::vec_op<LIMBS>(op, count, x, y, z, (cudaStream_t)stream);                                       \
+  }                                                                                                              \
+  extern "C" int zozaki_split_##SUF(int side, int64_t rows, int64_t cols, const double *X, int64_t ld,          \
+                                    void *slices, int32_t *E, void *stream) {                                   \
+    return mclu::ozaki_split<LIMBS>(side, rows, cols, X, ld, slices, E, (cudaStream_t)stream);                  \
   }

@@ -617,6 +617,11 @@ __global__ void k_rank1_adjoint(View lam, View x, View Ab, int64_t n) {
   stz<L>(Ab, i, j, z_neg<L>(z_mul<L>(l, xj)));
 }
 
+// Reports a nonzero tensor-core pipeline status through info (< 0).
+static __global__ void k_merge_status(const int *status, int *info) {
+  if (*status) *info = -1000 - *status;
+}
+
 // Elementwise operations (mclu_vec_op).
 template <int L>
 __global__ void k_vec_op(int op, int64_t count, const double *x, const double *y, double *z) {

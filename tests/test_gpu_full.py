@@ -1,5 +1,5 @@
 """Full-size checks at n = 4096 in the benchmark's launch configuration
-(blocked, nb = 64, 4M and 3M trailing update), by properties that hold at any
+(blocked, nb = 64 with the 4M and 3M updates, nb = 32 with the Ozaki update), by properties that hold at any
 size and that the oracle can evaluate one output at a time:
 
 * backward error with the exact residual: ||b - A x|| / (||A|| ||x||) <= 16 n u;
@@ -35,7 +35,8 @@ def _apply_pivots(A, ipiv):
     return P
 
 
-@pytest.mark.parametrize("prec,method", [("dd", "4m"), ("dd", "3m"), ("td", "4m"), ("qd", "4m")])
+@pytest.mark.parametrize("prec,method", [("dd", "4m"), ("dd", "3m"), ("td", "4m"), ("qd", "4m"),
+                                         ("dd", "ozaki"), ("td", "ozaki"), ("qd", "ozaki")])
 def test_full_size(api, orc, prec, method):
     import torch
     L = {"dd": 2, "td": 3, "qd": 4}[prec]
@@ -43,7 +44,7 @@ def test_full_size(api, orc, prec, method):
     A = inputs.gaussian_matrix(n, L, seed=1)
     b = inputs.complex_gaussian_vector(n, L, seed=2)
     Ad = dev(A)
-    LU, ipiv, info = api.lu_factor(Ad, method=method, nb=64)
+    LU, ipiv, info = api.lu_factor(Ad, method=method, nb=32 if method == "ozaki" else 64)
     x = api.lu_solve(LU, ipiv, dev(b))
     torch.cuda.synchronize()
     assert int(host(info)[0]) == 0
