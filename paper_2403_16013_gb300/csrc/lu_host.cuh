@@ -217,8 +217,8 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
         const int RT = (int)((jb + 31) / 32 * 32);
         const int CT = std::max(1, 256 / RT);
         View A12{Ap + jend * lda, lda, lda * n};
-        k_tri_block<L, true, true, false>
-            <<<(unsigned)cdiv(n2, CT), dim3(RT, CT), CT * 2 * L * sizeof(double), s>>>(A, j0, (int)jb, A12, n2);
+        k_tri_block<L, true, true, false><<<(unsigned)cdiv(n2, CT), dim3(RT, CT), CT * 2 * L * sizeof(double), s>>>(
+            A, j0, (int)jb, A12, n2, nullptr, 0);
         MCLU_LAUNCHED();
       }
       // A22 -= L21 U12
@@ -251,17 +251,18 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
 
 // Forward (LOWER) or backward substitution over all diagonal blocks of T on
 // the n x nrhs planes X.
+// rdiag: reciprocals of the diagonal (planes [2L][n]) when !UNIT.
 template <int L, bool LOWER, bool UNIT, bool CONJT>
-int tri_solve(View A, int64_t n, View X, int64_t nrhs, cudaStream_t s) {
+int tri_solve(View A, int64_t n, View X, int64_t nrhs, const double *rdiag, cudaStream_t s) {
   constexpr int BS = 32;
   const int64_t nblk = cdiv(n, BS);
+  const int CT = nrhs >= 8 ? 8 : (int)nrhs;
   for (int64_t q = 0; q < nblk; q++) {
     const int64_t b = LOWER ? q : nblk - 1 - q;
     const int64_t k0 = b * BS;
     const int bs = (int)std::min<int64_t>(BS, n - k0);
-    const int CT = 8;
     k_tri_block<L, LOWER, UNIT, CONJT>
-        <<<(unsigned)cdiv(nrhs, CT), dim3(BS, CT), CT * 2 * L * sizeof(double), s>>>(A, k0, bs, X, nrhs);
+        <<<(unsigned)cdiv(nrhs, CT), dim3(BS, CT), CT * 2 * L * sizeof(double), s>>>(A, k0, bs, X, nrhs, rdiag, n);
     MCLU_LAUNCHED();
     const int64_t r0 = LOWER ? k0 + bs : 0, r1 = LOWER ? n : k0;
     if (r1 > r0) {
@@ -292,9 +293,16 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
   View B{Bp, ldb, ldb * nrhs};
   Workspace w;
   const size_t perm_bytes = ((size_t)n * sizeof(int32_t) + 255) & ~(size_t)255;
-  MCLU_TRY(w.alloc(perm_bytes + (size_t)2 * L * n * nrhs * sizeof(double), s));
+  const size_t rdiag_bytes = ((size_t)2 * L * n * sizeof(double) + 255) & ~(size_t)255;
+  MCLU_TRY(w.alloc(perm_bytes + rdiag_bytes + (size_t)2 * L * n * nrhs * sizeof(double), s));
   int32_t *perm = (int32_t *)w.p;
-  View X{(double *)((char *)w.p + perm_bytes), n, n * nrhs};
+  double *rdiag = (double *)((char *)w.p + perm_bytes);
+  View X{(double *)((char *)w.p + perm_bytes + rdiag_bytes), n, n * nrhs};
+  if (!conj)
+    k_diag_recip<L, false><<<(unsigned)cdiv(n, 128), 128, 0, s>>>(A, n, rdiag, n);
+  else
+    k_diag_recip<L, true><<<(unsigned)cdiv(n, 128), 128, 0, s>>>(A, n, rdiag, n);
+  MCLU_LAUNCHED();
   const size_t smem_perm = (size_t)n * sizeof(int32_t);
   const int use_smem = smem_perm <= 200 * 1024 ? 1 : 0;
   if (use_smem) MCLU_TRY(cudaFuncSetAttribute(k_perm_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -304,18 +312,18 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
   if (!conj) {
     k_permute<L><<<pg, 256, 0, s>>>(B, X, perm, n, nrhs, 0);  // X = P B
     MCLU_LAUNCHED();
-    int rc = tri_solve<L, true, true, false>(A, n, X, nrhs, s);
+    int rc = tri_solve<L, true, true, false>(A, n, X, nrhs, nullptr, s);
     if (rc) return rc;
-    rc = tri_solve<L, false, false, false>(A, n, X, nrhs, s);
+    rc = tri_solve<L, false, false, false>(A, n, X, nrhs, rdiag, s);
     if (rc) return rc;
     MCLU_TRY(cudaMemcpy2DAsync(Bp, ldb * sizeof(double), X.p, n * sizeof(double), n * sizeof(double),
                                (size_t)2 * L * nrhs, cudaMemcpyDeviceToDevice, s));
   } else {
     MCLU_TRY(cudaMemcpy2DAsync(X.p, n * sizeof(double), Bp, ldb * sizeof(double), n * sizeof(double),
                                (size_t)2 * L * nrhs, cudaMemcpyDeviceToDevice, s));
-    int rc = tri_solve<L, true, false, true>(A, n, X, nrhs, s);  // U^H w = b
+    int rc = tri_solve<L, true, false, true>(A, n, X, nrhs, rdiag, s);  // U^H w = b
     if (rc) return rc;
-    rc = tri_solve<L, false, true, true>(A, n, X, nrhs, s);      // L^H z = w
+    rc = tri_solve<L, false, true, true>(A, n, X, nrhs, nullptr, s);    // L^H z = w
     if (rc) return rc;
     k_permute<L><<<pg, 256, 0, s>>>(X, B, perm, n, nrhs, 1);     // B = P^T z
     MCLU_LAUNCHED();

@@ -329,13 +329,14 @@ __global__ void k_laswp(View A, int64_t c0, int64_t c1, int64_t k0, int64_t k1, 
 }
 
 // Triangular block solve T x = b for the bs x bs diagonal block of A at
-// (k0, k0) on columns of X (rows k0..k0+bs-1).  T = A (LOWER: unit or not) or,
+// (k0, k0) on columns of X (rows k0..k0+bs-1); rdiag (planes [2L][rld])
+// holds 1/T_kk when the diagonal is not unit.  T = A (LOWER: unit or not) or,
 // with CONJT, T(r, k) = conj(A(k0+k, k0+r)).  Right-looking inside the block:
 // at step k the owner of row k finalises x_k (dividing by T_kk if !UNIT) and
 // every row below (LOWER) or above (!LOWER) subtracts T(r,k) x_k.
 // Block: (RT rows, CT columns); grid.x over column groups.
 template <int L, bool LOWER, bool UNIT, bool CONJT>
-__global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols) {
+__global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, const double *rdiag, int64_t rld) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int CT = blockDim.y;
   const int64_t c = (int64_t)blockIdx.x * CT + ty;
@@ -346,10 +347,15 @@ __global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols) {
   for (int s = 0; s < bs; s++) {
     const int k = LOWER ? s : bs - 1 - s;
     if (ok && tx == k) {
-      if (!UNIT) {
-        Z<L> d = ldz<L>(A, k0 + k, k0 + k);
-        if (CONJT) d = z_conj<L>(d);
-        x = z_div<L>(x, d);
+      if (!UNIT) {  // multiply by the precomputed reciprocal of T_kk
+        const int64_t kk = k0 + k;
+        Z<L> r;
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          r.re.x[q] = rdiag[(int64_t)q * rld + kk];
+          r.im.x[q] = rdiag[(int64_t)(L + q) * rld + kk];
+        }
+        x = z_mul<L>(x, r);
       }
 #pragma unroll
       for (int q = 0; q < L; q++) {
@@ -371,6 +377,21 @@ __global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols) {
     __syncthreads();
   }
   if (ok) stz<L>(X, k0 + tx, c, x);
+}
+
+// rdiag[k] = 1 / T_kk for the diagonal of A (CONJT: of A^H), planes [2L][ld].
+template <int L, bool CONJT>
+__global__ void k_diag_recip(View A, int64_t n, double *rdiag, int64_t ld) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  Z<L> d = ldz<L>(A, k, k);
+  if (CONJT) d = z_conj<L>(d);
+  const Z<L> r = z_inv<L>(d);
+#pragma unroll
+  for (int q = 0; q < L; q++) {
+    rdiag[(int64_t)q * ld + k] = r.re.x[q];
+    rdiag[(int64_t)(L + q) * ld + k] = r.im.x[q];
+  }
 }
 
 // X[r, c] -= sum_{k < bs} T(r, k0+k) X[k0+k, c] for rows r in [r0, r1), where
