@@ -12,6 +12,7 @@
 #include "../../include/mclu.h"
 #include "lu_kernels.cuh"
 #include "ozaki.cuh"
+#include "panel_coop.cuh"
 
 namespace mclu {
 
@@ -88,9 +89,62 @@ constexpr size_t getrf_ws_bytes(int64_t n, int nb, bool m3) {
   size_t b = 4 * 256;                                           // counter, info, zflag, recip
   b += ((nparts * L * sizeof(double)) + 255) & ~(size_t)255;   // part_key
   b += ((nparts * sizeof(int)) + 255) & ~(size_t)255;          // part_idx
+  b += ((nparts * 2 * L * sizeof(double)) + 255) & ~(size_t)255;  // part_rcp
   b += ((2 * 2 * L * (size_t)n * sizeof(double)) + 255) & ~(size_t)255;  // lbuf
   if (m3) b += 2 * (((size_t)n * nb * L * sizeof(double)) + 255);         // 3M pre-sums
   return b + 1024;
+}
+
+// Launch a triangular block solve, staging the triangle in shared memory
+// when it fits (raising the kernel's dynamic shared-memory limit once).
+template <int L, bool LOWER, bool UNIT, bool CONJT>
+int launch_tri_block(dim3 grid, dim3 block, cudaStream_t s, View A, int64_t k0, int bs, View X, int64_t ncols,
+                     const double *rdiag, int64_t rld, int64_t xrow0) {
+  const size_t staged = tri_block_smem<L>(bs, (int)block.y, true);
+  if (staged <= 200 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      MCLU_TRY(cudaFuncSetAttribute(k_tri_block<L, LOWER, UNIT, CONJT, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+    k_tri_block<L, LOWER, UNIT, CONJT, true><<<grid, block, staged, s>>>(A, k0, bs, X, ncols, rdiag, rld, xrow0);
+  } else {
+    k_tri_block<L, LOWER, UNIT, CONJT, false>
+        <<<grid, block, tri_block_smem<L>(bs, (int)block.y, false), s>>>(A, k0, bs, X, ncols, rdiag, rld, xrow0);
+  }
+  MCLU_LAUNCHED();
+  return 0;
+}
+
+// Cooperative panel factorisation.  Returns 0 (launched), 1 (the grid or its
+// shared memory does not fit: caller falls back to per-column launches) or a
+// CUDA error code.
+template <int L>
+int launch_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int32_t *ipiv, PanelWS<L> ws, CoopWS cw,
+                      size_t nparts, cudaStream_t s) {
+  static int sms = 0, per_sm = -1;
+  const int nb = (int)(jend - j0);
+  const int64_t m = n - j0;
+  if (sms == 0) sms = oz::sm_count();
+  int G = (int)std::min<int64_t>({(int64_t)sms, cdiv(m, 8), (int64_t)nparts});
+  if (G < 1) G = 1;
+  const int rpc = (int)cdiv(m, G);
+  const size_t smem = (size_t)rpc * nb * 2 * L * sizeof(double);
+  if (smem > 200 * 1024) return 1;
+  if (per_sm < 0) {
+    MCLU_TRY(cudaFuncSetAttribute(k_panel_coop<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    per_sm = 0;
+  }
+  int occ = 0;
+  MCLU_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_panel_coop<L>, COOP_T, smem));
+  if ((int64_t)occ * sms < G) return 1;
+  int64_t a_n = n, a_j0 = j0, a_jend = jend;
+  int a_rpc = rpc;
+  void *args[] = {&A, &a_n, &a_j0, &a_jend, &a_rpc, &ipiv, &ws, &cw};
+  MCLU_TRY(cudaLaunchCooperativeKernel((const void *)k_panel_coop<L>, dim3(G), dim3(COOP_T), args, smem, s));
+  note_launch();
+  return 0;
 }
 
 template <int L>
@@ -157,7 +211,9 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   const bool ozk = method == MCLU_METHOD_OZAKI;
   Workspace w;
   const size_t oz_need = ozk ? oz::ws_bytes<L>(n, n, nb) : 0;
-  const size_t ws_need = getrf_ws_bytes<L>(n, m3 ? nb : 0, m3) + oz_need;
+  const size_t ws_need = getrf_ws_bytes<L>(n, m3 ? nb : 0, m3) + oz_need +
+                         (ozk ? (size_t)2 * L * nb * nb * sizeof(double) + 256 : 0) +
+                         2 * (((size_t)2 * 2 * L * nb * sizeof(double) + 255) & ~(size_t)255);
   char *ws_base = nullptr;
   if (ext_ws) {
     if (ext_bytes < ws_need) return MCLU_ERR_SCRATCH_CAPACITY;
@@ -176,6 +232,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   size_t nparts = (size_t)cdiv(n, PANEL_T) + 1;
   ws.part_key = cv.take<double>(nparts * L);
   ws.part_idx = cv.take<int>(nparts);
+  ws.part_rcp = cv.take<double>(nparts * 2 * L);
   ws.lbuf = cv.take<double>(2 * 2 * L * (size_t)n);
   ws.lbuf_ld = n;
   double *sumL = nullptr, *sumU = nullptr;
@@ -184,6 +241,13 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     sumU = cv.take<double>((size_t)n * nb * L);
   }
   void *oz_ws = ozk ? (void *)cv.take<char>(oz_need) : nullptr;
+  CoopWS cw;
+  cw.bar_count = (unsigned *)(hdr + 640);
+  cw.bar_gen = (unsigned *)(hdr + 644);
+  cw.status = (int *)(hdr + 648);
+  cw.prow = cv.take<double>((size_t)2 * 2 * L * nb);
+  cw.srow = cv.take<double>((size_t)2 * 2 * L * nb);
+  double *winv = ozk ? cv.take<double>((size_t)2 * L * nb * nb) : nullptr;
   int *oz_status = ws.zflag + 1;  // spare word of the header block
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
   View A{Ap, lda, lda * n};
@@ -192,12 +256,17 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     const int64_t jb = std::min<int64_t>(nb, n - j0), jend = j0 + jb;
     {  // panel: rows [j0, n), columns [j0, jend)
       ProfScope ps(PK_PANEL, s);
-      k_pivot_first<L><<<(unsigned)cdiv(n - j0, SEARCH_T), SEARCH_T, 0, s>>>(A, n, j0, j0, jend, ipiv, ws);
-      MCLU_LAUNCHED();
-      for (int64_t j = j0; j < jend; j++) {
-        dim3 grid((unsigned)std::max<int64_t>(1, cdiv(n - j - 1, PANEL_T)), (unsigned)panel_colblocks(j, jend));
-        k_panel_step<L><<<grid, dim3(PANEL_T, PANEL_T), 0, s>>>(A, n, j, j0, jend, ipiv, ws);
+      int rc = launch_panel_coop<L>(A, n, j0, jend, ipiv, ws, cw, nparts, s);
+      if (rc == 1) {  // cooperative grid does not fit: one launch per column
+        k_pivot_first<L><<<(unsigned)cdiv(n - j0, SEARCH_T), SEARCH_T, 0, s>>>(A, n, j0, j0, jend, ipiv, ws);
         MCLU_LAUNCHED();
+        for (int64_t j = j0; j < jend; j++) {
+          dim3 grid((unsigned)std::max<int64_t>(1, cdiv(n - j - 1, PANEL_T)), (unsigned)panel_colblocks(j, jend));
+          k_panel_step<L><<<grid, dim3(PANEL_T, PANEL_T), 0, s>>>(A, n, j, j0, jend, ipiv, ws);
+          MCLU_LAUNCHED();
+        }
+      } else if (rc) {
+        return rc;
       }
     }
     if (j0 > 0) {  // apply the panel's swaps to the columns on its left
@@ -217,9 +286,24 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
         const int RT = (int)((jb + 31) / 32 * 32);
         const int CT = std::max(1, 256 / RT);
         View A12{Ap + jend * lda, lda, lda * n};
-        k_tri_block<L, true, true, false><<<(unsigned)cdiv(n2, CT), dim3(RT, CT), CT * 2 * L * sizeof(double), s>>>(
-            A, j0, (int)jb, A12, n2, nullptr, 0);
-        MCLU_LAUNCHED();
+        if (!ozk) {
+          int rc = launch_tri_block<L, true, true, false>(dim3((unsigned)cdiv(n2, CT)), dim3(RT, CT), s, A, j0, (int)jb,
+                                                          A12, n2, nullptr, 0, j0);
+          if (rc) return rc;
+        } else {
+          // W = L11^{-1} (unit lower, jb x jb) by the same block solve on the
+          // identity, then U12 = W A12 as an Ozaki product written in place
+          // (the operands are sliced before the product is stored).
+          View W{winv, jb, jb * jb};
+          k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(W, jb);
+          MCLU_LAUNCHED();
+          int rc0 = launch_tri_block<L, true, true, false>(dim3((unsigned)cdiv(jb, CT)), dim3(RT, CT), s, A, j0,
+                                                           (int)jb, W, jb, nullptr, 0, 0);
+          if (rc0) return rc0;
+          int rc = oz::gemm<L>(false, W, View{Ap + jend * lda + j0, lda, lda * n}, View{Ap + jend * lda + j0, lda, lda * n},
+                               jb, n2, jb, oz_ws, oz_status, s, note_launch);
+          if (rc) return rc;
+        }
       }
       // A22 -= L21 U12
       View L21{Ap + j0 * lda + jend, lda, lda * n};
@@ -241,10 +325,11 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
       if (rc) return rc;
     }
   }
-  if (ozk) {  // a timed-out tensor-core pipeline is reported through info
-    k_merge_status<<<1, 1, 0, s>>>(oz_status, ws.info);
-    MCLU_LAUNCHED();
-  }
+  // a timed-out tensor-core pipeline or grid barrier is reported through info
+  k_merge_status<<<1, 1, 0, s>>>(oz_status, ws.info);
+  MCLU_LAUNCHED();
+  k_merge_status<<<1, 1, 0, s>>>(cw.status, ws.info);
+  MCLU_LAUNCHED();
   if (info) MCLU_TRY(cudaMemcpyAsync(info, ws.info, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   return 0;
 }
@@ -261,13 +346,19 @@ int tri_solve(View A, int64_t n, View X, int64_t nrhs, const double *rdiag, cuda
     const int64_t b = LOWER ? q : nblk - 1 - q;
     const int64_t k0 = b * BS;
     const int bs = (int)std::min<int64_t>(BS, n - k0);
-    k_tri_block<L, LOWER, UNIT, CONJT>
-        <<<(unsigned)cdiv(nrhs, CT), dim3(BS, CT), CT * 2 * L * sizeof(double), s>>>(A, k0, bs, X, nrhs, rdiag, n);
-    MCLU_LAUNCHED();
+    int rc = launch_tri_block<L, LOWER, UNIT, CONJT>(dim3((unsigned)cdiv(nrhs, CT)), dim3(BS, CT), s, A, k0, bs, X,
+                                                     nrhs, rdiag, n, k0);
+    if (rc) return rc;
     const int64_t r0 = LOWER ? k0 + bs : 0, r1 = LOWER ? n : k0;
     if (r1 > r0) {
-      dim3 grid((unsigned)cdiv(r1 - r0, 32), (unsigned)cdiv(nrhs, 8));
-      k_gemv<L, CONJT><<<grid, dim3(32, 8), 0, s>>>(A, r0, r1, k0, bs, X, nrhs);
+      dim3 grid((unsigned)cdiv(r1 - r0, 32), (unsigned)nrhs);
+      static bool attr = false;
+      if (!attr) {
+        MCLU_TRY(cudaFuncSetAttribute(k_gemv<L, CONJT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)gemv_smem<L>()));
+        attr = true;
+      }
+      k_gemv<L, CONJT><<<grid, 256, gemv_smem<L>(), s>>>(A, r0, r1, k0, bs, X, nrhs);
       MCLU_LAUNCHED();
     }
   }

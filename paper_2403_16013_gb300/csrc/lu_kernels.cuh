@@ -35,6 +35,7 @@ struct PanelWS {
   double *recip;    // [2L] reciprocal of the current pivot (re limbs, im limbs)
   double *part_key; // [nparts][L]
   int *part_idx;    // [nparts]
+  double *part_rcp; // [nparts][2L] reciprocal of each partial's candidate
   double *lbuf;     // [2][2L][lbuf_ld] pending multipliers of a column (double buffered)
   int64_t lbuf_ld;
 };
@@ -95,7 +96,7 @@ template <int L>
 __device__ void finalize_pivot(View A, int64_t n, int64_t jp, int64_t j0, int64_t jend, int32_t *ipiv,
                                PanelWS<L> ws, int nparts, int pend, int tid, int nthr) {
   R<L> key = invalid_key<L>();
-  int idx = INT_MAX;
+  int idx = INT_MAX, part = -1;
   for (int q = tid; q < nparts; q += nthr) {
     R<L> k;
 #pragma unroll
@@ -104,9 +105,17 @@ __device__ void finalize_pivot(View A, int64_t n, int64_t jp, int64_t j0, int64_
     if (better<L>(k, i, key, idx)) {
       key = k;
       idx = i;
+      part = q;
     }
   }
+  __shared__ int s_part;
+  const int my_idx = idx;
   block_argmax<L>(key, idx, tid, nthr);
+  __shared__ int s_win;
+  if (tid == 0) s_win = idx;
+  __syncthreads();
+  if (my_idx == s_win && my_idx != INT_MAX) s_part = part;  // the thread that read the winning partial
+  __syncthreads();
   __shared__ int s_p, s_zero;
   if (tid == 0) {
     bool zero = !(key.x[0] > 0.0);
@@ -140,16 +149,35 @@ __device__ void finalize_pivot(View A, int64_t n, int64_t jp, int64_t j0, int64_
   }
   __syncthreads();
   if (tid == 0) {
-    if (!s_zero) {
-      Z<L> r = z_inv<L>(ldz<L>(A, jp, jp));
+    if (!s_zero) {  // the winning candidate computed its reciprocal already
 #pragma unroll
-      for (int l = 0; l < L; l++) {
-        ws.recip[l] = r.re.x[l];
-        ws.recip[L + l] = r.im.x[l];
-      }
+      for (int l = 0; l < 2 * L; l++) ws.recip[l] = __ldcg(ws.part_rcp + (int64_t)s_part * 2 * L + l);
     }
     *ws.counter = 0;
     __threadfence();
+  }
+}
+
+// Block argmax of (key, row) that also publishes the reciprocal of the
+// winner's value into the block's partial q.
+template <int L>
+__device__ void write_partial(R<L> key, int idx, const Z<L> &rcp, PanelWS<L> ws, int q, int tid, int nthr) {
+  const int my_idx = idx;
+  block_argmax<L>(key, idx, tid, nthr);
+  __shared__ int s_w;
+  if (tid == 0) {
+#pragma unroll
+    for (int l = 0; l < L; l++) ws.part_key[(int64_t)q * L + l] = key.x[l];
+    ws.part_idx[q] = idx;
+    s_w = idx;
+  }
+  __syncthreads();
+  if (my_idx == s_w && my_idx != INT_MAX) {
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+      ws.part_rcp[(int64_t)q * 2 * L + l] = rcp.re.x[l];
+      ws.part_rcp[(int64_t)q * 2 * L + L + l] = rcp.im.x[l];
+    }
   }
 }
 
@@ -175,16 +203,14 @@ __global__ void __launch_bounds__(SEARCH_T) k_pivot_first(View A, int64_t n, int
   const int64_t i = j + (int64_t)blockIdx.x * SEARCH_T + tid;
   R<L> key = invalid_key<L>();
   int idx = INT_MAX;
+  Z<L> rcp = z_zero<L>();
   if (i < n) {
-    key = pivot_key<L>(ldz<L>(A, i, j));
+    const Z<L> a = ldz<L>(A, i, j);
+    key = pivot_key<L>(a);
     idx = (int)i;
+    rcp = z_inv<L>(a);  // speculative: kept only if this row wins
   }
-  block_argmax<L>(key, idx, tid, SEARCH_T);
-  if (tid == 0) {
-#pragma unroll
-    for (int l = 0; l < L; l++) ws.part_key[(int64_t)blockIdx.x * L + l] = key.x[l];
-    ws.part_idx[blockIdx.x] = idx;
-  }
+  write_partial<L>(key, idx, rcp, ws, blockIdx.x, tid, SEARCH_T);
   if (arrive_last(ws.counter, gridDim.x, tid))
     finalize_pivot<L>(A, n, j, j0, jend, ipiv, ws, gridDim.x, -1, tid, SEARCH_T);
 }
@@ -293,16 +319,13 @@ __global__ void __launch_bounds__(PANEL_T *PANEL_T)
     if (blockIdx.y == 0) {
       R<L> key = invalid_key<L>();
       int idx = INT_MAX;
+      Z<L> rcp = z_zero<L>();
       if (ty == 0 && row_ok) {
         key = pivot_key<L>(updated);
         idx = (int)i;
+        rcp = z_inv<L>(updated);  // speculative: kept only if this row wins
       }
-      block_argmax<L>(key, idx, tid, PANEL_T * PANEL_T);
-      if (tid == 0) {
-#pragma unroll
-        for (int q = 0; q < L; q++) ws.part_key[(int64_t)blockIdx.x * L + q] = key.x[q];
-        ws.part_idx[blockIdx.x] = idx;
-      }
+      write_partial<L>(key, idx, rcp, ws, blockIdx.x, tid, PANEL_T * PANEL_T);
     }
     if (arrive_last(ws.counter, gridDim.x * gridDim.y, tid))
       finalize_pivot<L>(A, n, j + 1, j0, jend, ipiv, ws, gridDim.x, via_lbuf ? slot : -1, tid, PANEL_T * PANEL_T);
@@ -329,31 +352,55 @@ __global__ void k_laswp(View A, int64_t c0, int64_t c1, int64_t k0, int64_t k1, 
 }
 
 // Triangular block solve T x = b for the bs x bs diagonal block of A at
-// (k0, k0) on columns of X (rows k0..k0+bs-1); rdiag (planes [2L][rld])
-// holds 1/T_kk when the diagonal is not unit.  T = A (LOWER: unit or not) or,
+// (k0, k0) on columns of X (rows xrow0..xrow0+bs-1); rdiag (planes
+// [2L][rld]) holds 1/T_kk when the diagonal is not unit.  T = A (LOWER: unit or not) or,
 // with CONJT, T(r, k) = conj(A(k0+k, k0+r)).  Right-looking inside the block:
 // at step k the owner of row k finalises x_k (dividing by T_kk if !UNIT) and
 // every row below (LOWER) or above (!LOWER) subtracts T(r,k) x_k.
 // Block: (RT rows, CT columns); grid.x over column groups.
-template <int L, bool LOWER, bool UNIT, bool CONJT>
-__global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, const double *rdiag, int64_t rld) {
+template <int L, bool LOWER, bool UNIT, bool CONJT, bool STAGE>
+__global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, const double *rdiag, int64_t rld,
+                            int64_t xrow0) {
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int CT = blockDim.y;
+  const int RT = blockDim.x, CT = blockDim.y;
   const int64_t c = (int64_t)blockIdx.x * CT + ty;
   const bool ok = tx < bs && c < ncols;
-  extern __shared__ double s_x[];  // [CT][2L]
+  // dynamic shared memory: [STAGE: T block [bs][bs][2L] (row r, step k) and
+  // diagonal reciprocals [bs][2L]], exchange slots [CT][2L]
+  extern __shared__ double smem[];
+  double *sT = smem;
+  double *sR = sT + (STAGE ? (size_t)bs * bs * 2 * L : 0);
+  double *s_x = sR + (STAGE ? (size_t)bs * 2 * L : 0);
+  // stage the triangle once: T(r, k) = A(k0+r, k0+k) or conj(A(k0+k, k0+r))
+  for (int t = ty * RT + tx; STAGE && t < bs * bs; t += RT * CT) {
+    const int r = t % bs, kk = t / bs;
+    const bool need = LOWER ? (r > kk) : (r < kk);
+    Z<L> v = z_zero<L>();
+    if (need) v = CONJT ? z_conj<L>(ldz<L>(A, k0 + kk, k0 + r)) : ldz<L>(A, k0 + r, k0 + kk);
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      sT[((size_t)r * bs + kk) * 2 * L + q] = v.re.x[q];
+      sT[((size_t)r * bs + kk) * 2 * L + L + q] = v.im.x[q];
+    }
+  }
+  if (!UNIT && STAGE) {
+    for (int t = ty * RT + tx; t < bs * 2 * L; t += RT * CT) {
+      const int kk = t / (2 * L), q = t % (2 * L);
+      sR[t] = rdiag[(int64_t)q * rld + k0 + kk];
+    }
+  }
   Z<L> x;
-  if (ok) x = ldz<L>(X, k0 + tx, c);
+  if (ok) x = ldz<L>(X, xrow0 + tx, c);
+  __syncthreads();
   for (int s = 0; s < bs; s++) {
     const int k = LOWER ? s : bs - 1 - s;
     if (ok && tx == k) {
       if (!UNIT) {  // multiply by the precomputed reciprocal of T_kk
-        const int64_t kk = k0 + k;
         Z<L> r;
 #pragma unroll
         for (int q = 0; q < L; q++) {
-          r.re.x[q] = rdiag[(int64_t)q * rld + kk];
-          r.im.x[q] = rdiag[(int64_t)(L + q) * rld + kk];
+          r.re.x[q] = STAGE ? sR[k * 2 * L + q] : rdiag[(int64_t)q * rld + k0 + k];
+          r.im.x[q] = STAGE ? sR[k * 2 * L + L + q] : rdiag[(int64_t)(L + q) * rld + k0 + k];
         }
         x = z_mul<L>(x, r);
       }
@@ -365,8 +412,16 @@ __global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, c
     }
     __syncthreads();
     if (ok && (LOWER ? tx > k : tx < k)) {
-      Z<L> t = CONJT ? z_conj<L>(ldz<L>(A, k0 + k, k0 + tx)) : ldz<L>(A, k0 + tx, k0 + k);
-      Z<L> xk;
+      Z<L> t, xk;
+      if (STAGE) {
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          t.re.x[q] = sT[((size_t)tx * bs + k) * 2 * L + q];
+          t.im.x[q] = sT[((size_t)tx * bs + k) * 2 * L + L + q];
+        }
+      } else {
+        t = CONJT ? z_conj<L>(ldz<L>(A, k0 + k, k0 + tx)) : ldz<L>(A, k0 + tx, k0 + k);
+      }
 #pragma unroll
       for (int q = 0; q < L; q++) {
         xk.re.x[q] = s_x[ty * 2 * L + q];
@@ -376,7 +431,24 @@ __global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, c
     }
     __syncthreads();
   }
-  if (ok) stz<L>(X, k0 + tx, c, x);
+  if (ok) stz<L>(X, xrow0 + tx, c, x);
+}
+
+// Shared memory of k_tri_block for block size bs and CT columns.
+template <int L>
+constexpr size_t tri_block_smem(int bs, int CT, bool stage) {
+  return ((stage ? (size_t)bs * bs + bs : 0) + CT) * 2 * L * sizeof(double);
+}
+
+// X = identity (n x n planes, leading dimension ld).
+template <int L>
+__global__ void k_identity(View X, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int64_t i = t % n, j = t / n;
+  Z<L> z = z_zero<L>();
+  if (i == j) z.re.x[0] = 1.0;
+  stz<L>(X, i, j, z);
 }
 
 // rdiag[k] = 1 / T_kk for the diagonal of A (CONJT: of A^H), planes [2L][ld].
@@ -395,80 +467,88 @@ __global__ void k_diag_recip(View A, int64_t n, double *rdiag, int64_t ld) {
 }
 
 // X[r, c] -= sum_{k < bs} T(r, k0+k) X[k0+k, c] for rows r in [r0, r1), where
-// T(r, k) = A(r, k), or conj(A(k, r)) with CONJT.  One thread per (row, column)
-// accumulates the bs products on the leveled accumulator (one renormalisation
-// per output).  The A tile and the X block are staged through shared memory
-// 16 k at a time; with CONJT the A tile is read along its columns, which are
-// contiguous in memory, and transposed in shared memory.
+// T(r, k) = A(r, k), or conj(A(k, r)) with CONJT.  Eight lanes share a row:
+// lane g accumulates the products k = g, g+8, ... on the leveled accumulator
+// (short dependent chains), the eight partial accumulators are combined level
+// by level through warp shuffles, and lane 0 adds X[r, c] and renormalises.
+// The A tile (bs x 32 rows) and the X block are staged in shared memory; with
+// CONJT the A tile is read along its columns (contiguous in memory).
+template <int L>
+constexpr size_t gemv_smem() {
+  return (size_t)32 * (32 + 1) * 2 * L * sizeof(double);
+}
+
 template <int L, bool CONJT>
 __global__ void __launch_bounds__(256) k_gemv(View A, int64_t r0, int64_t r1, int64_t k0, int bs, View X,
                                               int64_t ncols) {
-  constexpr int TR = 32, TCC = 8, KC = 16;
-  __shared__ double sA[KC][TR][2 * L];
-  __shared__ double sX[KC][TCC][2 * L];
-  const int tx = threadIdx.x, ty = threadIdx.y;  // (32, 8)
-  const int tid = ty * TR + tx;
-  const int64_t r = r0 + (int64_t)blockIdx.x * TR + tx;
-  const int64_t c = (int64_t)blockIdx.y * TCC + ty;
+  constexpr int TR = 32, G = 8, BSM = 32;
+  extern __shared__ double gsm[];  // sA [BSM][TR][2L], then sX [BSM][2L]
+  double(*sA)[TR][2 * L] = reinterpret_cast<double(*)[TR][2 * L]>(gsm);
+  double(*sX)[2 * L] = reinterpret_cast<double(*)[2 * L]>(gsm + (size_t)BSM * TR * 2 * L);
+  const int tid = threadIdx.x;
+  const int g = tid & (G - 1), rloc = tid >> 3;  // 8 lanes per row, 32 rows per CTA
+  const int64_t r = r0 + (int64_t)blockIdx.x * TR + rloc;
+  const int64_t c = blockIdx.y;
+  for (int t = tid; t < bs * TR; t += 256) {
+    int kq, rq;
+    if (CONJT) {
+      kq = t % bs;
+      rq = t / bs;
+    } else {
+      rq = t % TR;
+      kq = t / TR;
+    }
+    const int64_t gr = r0 + (int64_t)blockIdx.x * TR + rq, gk = k0 + kq;
+    Z<L> v = z_zero<L>();
+    if (gr < r1) v = CONJT ? z_conj<L>(ldz<L>(A, gk, gr)) : ldz<L>(A, gr, gk);
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      sA[kq][rq][q] = v.re.x[q];
+      sA[kq][rq][L + q] = v.im.x[q];
+    }
+  }
+  for (int t = tid; t < bs; t += 256) {
+    Z<L> v = ldz<L>(X, k0 + t, c);
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      sX[t][q] = v.re.x[q];
+      sX[t][L + q] = v.im.x[q];
+    }
+  }
+  __syncthreads();
   Acc<L> are, aim;
-  const bool ok = r < r1 && c < ncols;
-  if (ok) {
-    Z<L> x0 = ldz<L>(X, r, c);
-    are.set(x0.re);
-    aim.set(x0.im);
+  are.zero();
+  aim.zero();
+  for (int kq = g; kq < bs; kq += G) {
+    R<L> ar, ai, xr, xi;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      ar.x[q] = sA[kq][rloc][q];
+      ai.x[q] = sA[kq][rloc][L + q];
+      xr.x[q] = sX[kq][q];
+      xi.x[q] = sX[kq][L + q];
+    }
+    are.template add_prod<true>(ar, xr);
+    are.template add_prod<false>(ai, xi);
+    aim.template add_prod<true>(ar, xi);
+    aim.template add_prod<true>(ai, xr);
   }
-  for (int kk = 0; kk < bs; kk += KC) {
-    // stage A tile: KC x TR elements
-    for (int t = tid; t < KC * TR; t += 256) {
-      int kq, rq;
-      if (CONJT) {  // consecutive threads walk k (contiguous in column r of A)
-        kq = t % KC;
-        rq = t / KC;
-      } else {      // consecutive threads walk r (contiguous in column k of A)
-        rq = t % TR;
-        kq = t / TR;
-      }
-      const int64_t gr = r0 + (int64_t)blockIdx.x * TR + rq, gk = k0 + kk + kq;
-      Z<L> v = z_zero<L>();
-      if (gr < r1 && kk + kq < bs) v = CONJT ? z_conj<L>(ldz<L>(A, gk, gr)) : ldz<L>(A, gr, gk);
+  // combine the 8 partial accumulators of this row (lanes g = 0..7)
 #pragma unroll
-      for (int q = 0; q < L; q++) {
-        sA[kq][rq][q] = v.re.x[q];
-        sA[kq][rq][L + q] = v.im.x[q];
-      }
-    }
-    for (int t = tid; t < KC * TCC; t += 256) {
-      const int kq = t % KC, cq = t / KC;
-      const int64_t gc = (int64_t)blockIdx.y * TCC + cq;
-      Z<L> v = z_zero<L>();
-      if (gc < ncols && kk + kq < bs) v = ldz<L>(X, k0 + kk + kq, gc);
+  for (int off = G / 2; off > 0; off >>= 1) {
+    Acc<L> ore, oim;
 #pragma unroll
-      for (int q = 0; q < L; q++) {
-        sX[kq][cq][q] = v.re.x[q];
-        sX[kq][cq][L + q] = v.im.x[q];
-      }
+    for (int q = 0; q < L; q++) {
+      ore.s[q] = __shfl_down_sync(0xffffffffu, are.s[q], off, G);
+      oim.s[q] = __shfl_down_sync(0xffffffffu, aim.s[q], off, G);
     }
-    __syncthreads();
-    if (ok) {
-      const int kmax = min(KC, bs - kk);
-      for (int kq = 0; kq < kmax; kq++) {
-        R<L> ar, ai, xr, xi;
-#pragma unroll
-        for (int q = 0; q < L; q++) {
-          ar.x[q] = sA[kq][tx][q];
-          ai.x[q] = sA[kq][tx][L + q];
-          xr.x[q] = sX[kq][ty][q];
-          xi.x[q] = sX[kq][ty][L + q];
-        }
-        are.template add_prod<true>(ar, xr);
-        are.template add_prod<false>(ai, xi);
-        aim.template add_prod<true>(ar, xi);
-        aim.template add_prod<true>(ai, xr);
-      }
-    }
-    __syncthreads();
+    are.add_acc(ore, false);
+    aim.add_acc(oim, false);
   }
-  if (ok) {
+  if (g == 0 && r < r1) {
+    const Z<L> x0 = ldz<L>(X, r, c);
+    are.add(x0.re);
+    aim.add(x0.im);
     Z<L> z;
     z.re = are.result();
     z.im = aim.result();

@@ -460,12 +460,43 @@ __device__ __forceinline__ R<L> z_norm2(const Z<L> &a) {
   return t.result();
 }
 
+// 1/d by Newton's iteration r <- r + r (1 - d r) from the binary64
+// reciprocal of the leading limb: one step reaches double-double accuracy,
+// a second step (in L-limb arithmetic) triple/quad-double accuracy.  Shorter
+// dependent chains than long division, which matters on the latency-bound
+// panel path.
+template <int L>
+__device__ __forceinline__ R<L> r_recip(const R<L> &d) {
+  const double r0 = __ddiv_rn(1.0, d.x[0]);
+  // e = 1 - d r0 (leveled, L limbs), then r = r0 + r0 e
+  Acc<L> t;
+  t.zero();
+  t.s[0] = 1.0;
+  t.add_prod1(flip(r0), d);
+  const R<L> e = t.result();
+  Acc<L> u;
+  u.zero();
+  u.s[0] = r0;
+  u.add_prod1(r0, e);
+  R<L> r = u.result();
+  if constexpr (L >= 3) {
+    Acc<L> t2;
+    t2.zero();
+    t2.s[0] = 1.0;
+    t2.template add_prod<true>(d, r);
+    const R<L> e2 = t2.result();
+    Acc<L> u2;
+    u2.set(r);
+    u2.add_prod(r, e2);
+    r = u2.result();
+  }
+  return r;
+}
+
 // 1/(a + bi) = (a - bi) / (a^2 + b^2)
 template <int L>
 __device__ __forceinline__ Z<L> z_inv(const Z<L> &a) {
-  R<L> one = r_zero<L>();
-  one.x[0] = 1.0;
-  R<L> rinv = r_div<L>(one, z_norm2<L>(a));
+  const R<L> rinv = r_recip<L>(z_norm2<L>(a));
   Z<L> r;
   r.re = r_mul<L>(a.re, rinv);
   r.im = r_neg<L>(r_mul<L>(a.im, rinv));

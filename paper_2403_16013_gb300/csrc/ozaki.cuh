@@ -52,18 +52,19 @@ template <int L>
 struct Cfg;
 // beta: digit bits; S: slices; N: realified columns per tile; FW: 32-bit words of
 // the fold accumulator F; TW: words of the split integer T; RW: words of the
-// final C - P frame.
+// final C - P frame; GS: diagonals pre-combined in int64 (GS diagonals of at
+// most 2^24, shifted by beta each, stay below 2^60).
 template <>
 struct Cfg<2> {
-  static constexpr int BETA = 8, S = 14, N = 32, FW = 5, TW = 4, RW = 6;
+  static constexpr int BETA = 8, S = 14, N = 32, FW = 5, TW = 4, RW = 6, GS = 5;
 };
 template <>
 struct Cfg<3> {
-  static constexpr int BETA = 7, S = 24, N = 16, FW = 7, TW = 6, RW = 8;
+  static constexpr int BETA = 7, S = 24, N = 16, FW = 7, TW = 6, RW = 8, GS = 6;
 };
 template <>
 struct Cfg<4> {
-  static constexpr int BETA = 7, S = 32, N = 16, FW = 9, TW = 8, RW = 10;
+  static constexpr int BETA = 7, S = 32, N = 16, FW = 9, TW = 8, RW = 10, GS = 6;
 };
 
 constexpr int KC = 64;         // realified K per chunk (32 complex columns of A)
@@ -353,70 +354,6 @@ __global__ void k_oz_split_b(View X, int64_t k, int64_t n, const int *Eb, __nv_b
 
 // ------------------------------------------------------ final C - P step --
 
-// Round the signed integer R (W words, value R 2^lsb) to the nearest binary64
-// (ties to even), subtract that double from R (exactly) and return it.
-// Values stay in the normal binary64 range (documented input range).
-template <int W>
-__device__ __forceinline__ double take_limb(uint32_t (&R)[W], int lsb) {
-  const bool neg = (int32_t)R[W - 1] < 0;
-  uint32_t a[W];  // |R|
-  {
-    uint64_t carry = neg ? 1ULL : 0ULL;
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-      const uint64_t t = (uint64_t)(neg ? ~R[w] : R[w]) + carry;
-      a[w] = (uint32_t)t;
-      carry = t >> 32;
-    }
-  }
-  int top = -1;  // highest set bit of |R|
-#pragma unroll
-  for (int w = 0; w < W; w++)
-    if (a[w]) top = 32 * w + 31 - __clz(a[w]);
-  if (top < 0) return 0.0;
-  uint64_t mant;
-  int e0;  // value = mant * 2^(e0 + lsb)
-  if (top <= 52) {  // fits exactly
-    mant = (uint64_t)a[0] | ((W > 1 ? (uint64_t)a[1] : 0ULL) << 32);
-    e0 = 0;
-  } else {
-    const int lo = top - 52;  // lowest kept bit
-    mant = 0;
-    uint32_t round = 0, sticky = 0;
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-      const uint32_t v = a[w];
-      const int sh = 32 * w - lo;  // where bit 0 of this word lands in the mantissa
-      if (sh >= 0) {
-        if (sh < 64) mant |= (uint64_t)v << sh;
-      } else if (sh > -32) {
-        mant |= (uint64_t)(v >> (-sh));
-      }
-      const int rb = lo - 1 - 32 * w;  // round bit index inside this word
-      if (rb >= 0 && rb < 32) round = (v >> rb) & 1u;
-      if (rb >= 32) sticky |= v;                       // word entirely below the round bit
-      else if (rb > 0) sticky |= v & ((1u << rb) - 1u);
-    }
-    mant &= (1ULL << 53) - 1ULL;
-    if (round && (sticky || (mant & 1ULL))) mant += 1ULL;
-    e0 = lo;
-    if (mant >> 53) {  // rounding carried into a new bit
-      mant >>= 1;
-      e0 += 1;
-    }
-  }
-  // normalise to 53 significant bits
-  const int msb = 63 - __clzll((long long)mant);
-  const int up = 52 - msb;
-  const uint64_t mm = mant << up;
-  const int ex = e0 + lsb - up;  // value = mm * 2^ex, 2^52 <= mm < 2^53
-  const unsigned long long bits = ((unsigned long long)(neg ? 1 : 0) << 63) |
-                                  ((unsigned long long)(ex + 52 + 1023) << 52) | (mm & 0xFFFFFFFFFFFFFULL);
-  // R -= d: add (-d) = mm * 2^(ex - lsb) with the opposite sign (exact: ex >= lsb)
-  add_shifted<W>(R, mm, ex - lsb, !neg);
-  return __longlong_as_double((long long)bits);
-}
-
 // Word idx of a register array (select chain, no dynamic indexing).
 template <int W>
 __device__ __forceinline__ uint32_t word_at(const uint32_t (&F)[W], int idx, uint32_t fill) {
@@ -426,32 +363,86 @@ __device__ __forceinline__ uint32_t word_at(const uint32_t (&F)[W], int idx, uin
   return r;
 }
 
-// F += D * 2^SHIFT for a compile-time shift (F: W words, two's complement).
+// F += G * 2^SHIFT for a signed 64-bit G with |G| < 2^60 (compile-time shift).
 template <int W, int SHIFT>
-__device__ __forceinline__ void fold(uint32_t (&F)[W], int32_t D) {
+__device__ __forceinline__ void fold64(uint32_t (&F)[W], long long G) {
   constexpr int WS = SHIFT / 32, BS = SHIFT % 32;
-  const long long v = (long long)D << BS;  // |D| < 2^25: fits in 57 bits
-  const uint32_t w0 = (uint32_t)v, w1 = (uint32_t)((unsigned long long)v >> 32);
-  const uint32_t sx = v < 0 ? 0xFFFFFFFFu : 0u;
+  const uint32_t sx = G < 0 ? 0xFFFFFFFFu : 0u;
+  // G << BS as a 96-bit two's complement value (w0, w1, w2)
+  const unsigned long long ug = (unsigned long long)G;
+  const uint32_t g0 = (uint32_t)ug, g1 = (uint32_t)(ug >> 32);
+  const uint32_t w0 = BS ? (g0 << BS) : g0;
+  const uint32_t w1 = BS ? ((g1 << BS) | (g0 >> (32 - BS))) : g1;
+  const uint32_t w2 = BS ? ((sx << BS) | (g1 >> (32 - BS))) : sx;
   uint64_t carry = 0;
 #pragma unroll
   for (int w = WS; w < W; w++) {
-    const uint32_t add = (w == WS) ? w0 : (w == WS + 1) ? w1 : sx;
+    const uint32_t add = (w == WS) ? w0 : (w == WS + 1) ? w1 : (w == WS + 2) ? w2 : sx;
     const uint64_t t = (uint64_t)F[w] + add + carry;
     F[w] = (uint32_t)t;
     carry = t >> 32;
   }
 }
 
-// out = C - F 2^eF (BETA) or F 2^eF, rounded to L limbs.
+// Per-thread scratch in shared memory, interleaved so that the threads of a
+// warp touch consecutive words (no bank conflicts).  Runtime-indexed word
+// accesses go here (load/store pipe) instead of register select chains.
+struct Scratch {
+  uint32_t *p;
+  int stride;
+  __device__ __forceinline__ uint32_t &operator[](int w) const { return p[w * stride]; }
+};
+
+// acc (RW words, two's complement, registers) += sign * trunc(mant * 2^s)
+// with the runtime placement done through the scratch.
+template <int RW>
+__device__ __forceinline__ void add_limb(uint32_t (&acc)[RW], uint64_t mant, int s, bool neg, const Scratch &sc) {
+  if (mant == 0) return;
+  uint32_t t0, t1, t2;
+  int ws;
+  if (s < 0) {
+    if (s <= -64) return;
+    const uint64_t v = mant >> (-s);
+    t0 = (uint32_t)v;
+    t1 = (uint32_t)(v >> 32);
+    t2 = 0;
+    ws = 0;
+  } else {
+    ws = s >> 5;
+    const int bs = s & 31;
+    const uint64_t lo = mant << bs;
+    t0 = (uint32_t)lo;
+    t1 = (uint32_t)(lo >> 32);
+    t2 = bs ? (uint32_t)(mant >> (64 - bs)) : 0u;
+  }
+#pragma unroll
+  for (int w = 0; w < RW + 2; w++) sc[w] = 0u;
+  sc[ws] = t0;
+  sc[ws + 1] = t1;
+  sc[ws + 2] = t2;
+  uint64_t carry = neg ? 1ULL : 0ULL;
+#pragma unroll
+  for (int w = 0; w < RW; w++) {
+    uint32_t v = sc[w];
+    if (neg) v = ~v;
+    const uint64_t t = (uint64_t)acc[w] + v + carry;
+    acc[w] = (uint32_t)t;
+    carry = t >> 32;
+  }
+}
+
+// out = C - F 2^eF (BETA) or F 2^eF, rounded to L limbs (greedy round to
+// nearest even).  The remainder is kept in sign-magnitude form; every limb
+// reads a 96-bit window at the leading word, rounds, and keeps the bits below
+// the rounding position (complemented if it rounded up).
 template <int L, int FW, int RW, bool BETA>
-__device__ __forceinline__ void finish(const uint32_t (&F)[FW], int eF, const double (&c)[L], double (&out)[L]) {
-  // magnitude of F
+__device__ __forceinline__ void finish2(const uint32_t (&F)[FW], int eF, const double (&c)[L], double (&out)[L],
+                                        const Scratch &sc) {
   const bool fneg = (int32_t)F[FW - 1] < 0;
   int topF = -1;
 #pragma unroll
   for (int w = 0; w < FW; w++) {
-    const uint32_t v = fneg ? ~F[w] : F[w];  // |F| - 1 for negatives: same top bit up to one
+    const uint32_t v = fneg ? ~F[w] : F[w];
     if (v) topF = 32 * w + 31 - __clz(v);
   }
   int top = (topF >= 0) ? eF + topF + 1 : -100000;
@@ -464,33 +455,151 @@ __device__ __forceinline__ void finish(const uint32_t (&F)[FW], int eF, const do
   top += 2;
   const int lsb = max(eF, top - (32 * RW - 2));
   uint32_t R[RW];
+  if (lsb == eF) {  // common case: F enters the frame unshifted
+    const uint32_t sx = fneg ? 0xFFFFFFFFu : 0u;
+    uint64_t carry = BETA ? 1ULL : 0ULL;  // R = -F (BETA) or F
 #pragma unroll
-  for (int w = 0; w < RW; w++) R[w] = 0;
+    for (int w = 0; w < RW; w++) {
+      const uint32_t v = (w < FW) ? F[w] : sx;
+      const uint64_t t = (uint64_t)(BETA ? ~v : v) + carry;
+      R[w] = (uint32_t)t;
+      carry = t >> 32;
+    }
+  } else {  // C dominates: F shifted right into C's frame (truncation below lsb)
+#pragma unroll
+    for (int w = 0; w < RW; w++) R[w] = 0;
+    const int s = lsb - eF, ws = s >> 5, bs = s & 31;
+    const uint32_t sx = fneg ? 0xFFFFFFFFu : 0u;
+    uint64_t carry = BETA ? 1ULL : 0ULL;
+#pragma unroll
+    for (int w = 0; w < RW; w++) {
+      const uint32_t lo = word_at<FW>(F, w + ws, sx);
+      const uint32_t hi = word_at<FW>(F, w + ws + 1, sx);
+      const uint32_t v = bs ? ((lo >> bs) | (hi << (32 - bs))) : lo;
+      const uint64_t t = (uint64_t)R[w] + (uint32_t)(BETA ? ~v : v) + carry;
+      R[w] = (uint32_t)t;
+      carry = t >> 32;
+    }
+  }
   if (BETA) {
 #pragma unroll
     for (int l = 0; l < L; l++) {
       if (is_zero(c[l])) continue;
       const Unpacked u = unpack(c[l]);
-      add_shifted<RW>(R, u.mant, u.e - lsb, u.neg);
+      add_limb<RW>(R, u.mant, u.e - lsb, u.neg, sc);
     }
   }
-  // R -= F >> (lsb - eF) (BETA) or R += F >> (lsb - eF): arithmetic shift,
-  // exact when lsb == eF; subtraction adds ~x + 1
-  const int s = lsb - eF;
-  const int ws = s >> 5, bs = s & 31;
-  const uint32_t sx = fneg ? 0xFFFFFFFFu : 0u;
-  uint64_t carry = BETA ? 1ULL : 0ULL;
+  // sign-magnitude
+  bool neg = (int32_t)R[RW - 1] < 0;
+  {
+    uint64_t carry = neg ? 1ULL : 0ULL;
 #pragma unroll
-  for (int w = 0; w < RW; w++) {
-    const uint32_t lo = word_at<FW>(F, w + ws, sx);
-    const uint32_t hi = word_at<FW>(F, w + ws + 1, sx);
-    const uint32_t v = bs ? ((lo >> bs) | (hi << (32 - bs))) : lo;
-    const uint64_t t = (uint64_t)R[w] + (uint32_t)(BETA ? ~v : v) + carry;
-    R[w] = (uint32_t)t;
-    carry = t >> 32;
+    for (int w = 0; w < RW; w++) {
+      const uint64_t t = (uint64_t)(neg ? ~R[w] : R[w]) + carry;
+      R[w] = (uint32_t)t;
+      carry = t >> 32;
+    }
   }
 #pragma unroll
-  for (int l = 0; l < L; l++) out[l] = take_limb<RW>(R, lsb);
+  for (int l = 0; l < L; l++) {
+    int tw = -1;
+#pragma unroll
+    for (int w = 0; w < RW; w++)
+      if (R[w]) tw = w;
+    if (tw < 0) {
+      out[l] = 0.0;
+      continue;
+    }
+    // scratch: words of |R| and prefix ORs (sticky below the window)
+    uint32_t orb = 0;
+#pragma unroll
+    for (int w = 0; w < RW; w++) {
+      sc[w] = R[w];
+      sc[RW + w] = orb;  // OR of words [0, w)
+      orb |= R[w];
+    }
+    const uint32_t h = sc[tw];
+    const uint32_t m = tw >= 1 ? sc[tw - 1] : 0u;
+    const uint32_t q = tw >= 2 ? sc[tw - 2] : 0u;
+    const uint32_t below = tw >= 2 ? sc[RW + tw - 2] : 0u;
+    const int z = __clz(h);  // h != 0
+    // 96-bit window (h:m:q) << z: leading bit at window bit 95
+    const uint32_t W2 = z ? (h << z) | (m >> (32 - z)) : h;
+    const uint32_t W1 = z ? (m << z) | (q >> (32 - z)) : m;
+    const uint32_t W0 = z ? (q << z) : q;
+    uint64_t mant = ((uint64_t)W2 << 21) | (W1 >> 11);          // bits 95..43 (53 bits)
+    const uint32_t rbit = (W1 >> 10) & 1u;                      // bit 42
+    const uint32_t sticky = (W1 & 0x3FFu) | W0 | below;         // bits 41..0 and lower words
+    const int top_bit = 32 * tw + 31 - z;                       // position of the leading bit in R
+    const int lo = top_bit - 52;                                // position of the mantissa LSB
+    bool up = false;
+    if (lo > 0) {
+      up = rbit && (sticky || (mant & 1ULL));
+    } else {  // the whole value fits: exact
+      mant = 0;
+#pragma unroll
+      for (int w = 0; w < 2 && w < RW; w++) mant |= (uint64_t)R[w] << (32 * w);
+    }
+    int ex = (lo > 0 ? lo : 0) + lsb;  // value = mant * 2^ex
+    uint64_t mm = mant + (up ? 1ULL : 0ULL);
+    if (mm >> 53) {
+      mm >>= 1;
+      ex += 1;
+    }
+    {  // normalise (only the exact small case can have fewer than 53 bits)
+      const int msb = 63 - __clzll((long long)mm);
+      mm <<= (52 - msb);
+      ex -= (52 - msb);
+    }
+    const unsigned long long bits = ((unsigned long long)(neg ? 1 : 0) << 63) |
+                                    ((unsigned long long)(ex + 52 + 1023) << 52) | (mm & 0xFFFFFFFFFFFFFULL);
+    out[l] = __longlong_as_double((long long)bits);
+    // remainder: the bits of |R| below lo, complemented within lo bits if rounded up
+    if (lo <= 0) {
+#pragma unroll
+      for (int w = 0; w < RW; w++) R[w] = 0;
+    } else {
+      const int lw = lo >> 5, lb = lo & 31;
+      const uint32_t lmask = lb ? ((1u << lb) - 1u) : 0u;
+#pragma unroll
+      for (int w = 0; w < RW; w++) R[w] = (w < lw) ? R[w] : (w == lw ? (R[w] & lmask) : 0u);
+      if (up) {  // 2^lo - rest
+        uint64_t carry = 1;
+#pragma unroll
+        for (int w = 0; w < RW; w++) {
+          const uint32_t inv = (w < lw) ? ~R[w] : (w == lw ? (~R[w] & lmask) : 0u);
+          const uint64_t t = (uint64_t)inv + carry;
+          R[w] = (w < lw) ? (uint32_t)t : (w == lw ? ((uint32_t)t & lmask) : 0u);
+          carry = (w < lw) ? (t >> 32) : 0;
+        }
+        neg = !neg;
+      }
+    }
+  }
+}
+
+// Fold diagonals D0 .. D0+G-1 (G = min(GS, S - D0)) of the TMEM accumulators
+// into F: G_c = sum_t D_{D0+t} 2^(beta (G-1-t)) exactly in int64, then one
+// multiword addition at shift beta (S - D0 - G).
+template <int L, int NH, int D0>
+__device__ __forceinline__ void fold_diagonals(uint32_t (&F)[NH][Cfg<L>::FW], uint32_t tbase) {
+  constexpr int S = Cfg<L>::S, N = Cfg<L>::N, BETA = Cfg<L>::BETA, FW = Cfg<L>::FW;
+  constexpr int GS = Cfg<L>::GS;
+  constexpr int G = (S - D0) < GS ? (S - D0) : GS;
+  long long g[NH];
+#pragma unroll
+  for (int cc = 0; cc < NH; cc++) g[cc] = 0;
+#pragma unroll
+  for (int t = 0; t < G; t++) {
+    uint32_t v[NH];
+    tmem_ld<NH>(tbase + (uint32_t)((D0 + t) * N), v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int cc = 0; cc < NH; cc++) g[cc] = g[cc] * (1LL << BETA) + (long long)__float2int_rz(__uint_as_float(v[cc]));
+  }
+#pragma unroll
+  for (int cc = 0; cc < NH; cc++) fold64<FW, BETA *(S - D0 - G)>(F[cc], g[cc]);
+  if constexpr (D0 + G < S) fold_diagonals<L, NH, D0 + G>(F, tbase);
 }
 
 // ---------------------------------------------------------------- GEMM --
@@ -611,6 +720,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {  // ---------------------------------------------------- epilogue
     const int quarter = warp & 3, half = (warp - 2) >> 2;
     const int row = quarter * 32 + lane;
+    const int etid = threadIdx.x - 64;  // 0 .. 255
+    const Scratch sc{reinterpret_cast<uint32_t *>(sA + NST * A_BYTES) + etid, EPI_WARPS * 32};
     const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * NH);
     uint32_t r = 0;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
@@ -635,22 +746,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
         tc_fence_after();
         // diagonal d sits in TMEM columns [d N, d N + N)
-#define MCLU_FOLD_DIAG(D)                                                   \
-  if constexpr ((D) < S) {                                                  \
-    uint32_t v[NH];                                                         \
-    tmem_ld<NH>(tbase + (uint32_t)((D) * N), v);                            \
-    tmem_wait_ld();                                                         \
-    _Pragma("unroll") for (int cc = 0; cc < NH; cc++)                       \
-        fold<FW, BETA_B *(S - 1 - (D))>(F[cc], __float2int_rz(__uint_as_float(v[cc]))); \
-  }
-        MCLU_FOLD_DIAG(0) MCLU_FOLD_DIAG(1) MCLU_FOLD_DIAG(2) MCLU_FOLD_DIAG(3) MCLU_FOLD_DIAG(4)
-        MCLU_FOLD_DIAG(5) MCLU_FOLD_DIAG(6) MCLU_FOLD_DIAG(7) MCLU_FOLD_DIAG(8) MCLU_FOLD_DIAG(9)
-        MCLU_FOLD_DIAG(10) MCLU_FOLD_DIAG(11) MCLU_FOLD_DIAG(12) MCLU_FOLD_DIAG(13) MCLU_FOLD_DIAG(14)
-        MCLU_FOLD_DIAG(15) MCLU_FOLD_DIAG(16) MCLU_FOLD_DIAG(17) MCLU_FOLD_DIAG(18) MCLU_FOLD_DIAG(19)
-        MCLU_FOLD_DIAG(20) MCLU_FOLD_DIAG(21) MCLU_FOLD_DIAG(22) MCLU_FOLD_DIAG(23) MCLU_FOLD_DIAG(24)
-        MCLU_FOLD_DIAG(25) MCLU_FOLD_DIAG(26) MCLU_FOLD_DIAG(27) MCLU_FOLD_DIAG(28) MCLU_FOLD_DIAG(29)
-        MCLU_FOLD_DIAG(30) MCLU_FOLD_DIAG(31)
-#undef MCLU_FOLD_DIAG
+        fold_diagonals<L, NH, 0>(F, tbase);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar_accempty);
@@ -679,7 +775,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int c2 = 0; c2 < NH; c2++) v = (c2 == cc) ? F[c2][w] : v;
             f[w] = v;
           }
-          finish<L, FW, RW, BETA>(f, eF, cv, ov);
+          finish2<L, FW, RW, BETA>(f, eF, cv, ov, sc);
 #pragma unroll
           for (int l = 0; l < L; l++) cp[(int64_t)l * C.ps] = ov[l];
         }
@@ -798,8 +894,9 @@ int gemm(bool beta, View A, View B, View C, int64_t m, int64_t n, int64_t k, voi
   rc = make_map(&tmB, w + z.a_bytes, (uint64_t)z.nchunks * Cfg<L>::S * z.Npad, Cfg<L>::N);
   if (rc) return rc;
   constexpr int A_BYTES = BM * KC * 2, B_BYTES = Cfg<L>::S * Cfg<L>::N * KC * 2;
+  constexpr int SCR_BYTES = (2 * Cfg<L>::RW + 2) * EPI_WARPS * 32 * 4;  // epilogue scratch
   // at least ~116 KB so that a single CTA (and its 512 TMEM columns) fits per SM
-  const int smem = std::max(B_BYTES + NST * A_BYTES + 1024, 116 * 1024);
+  const int smem = std::max(B_BYTES + NST * A_BYTES + SCR_BYTES + 1024, 116 * 1024);
   const int64_t tiles = ((m + BM - 1) / BM) * (z.Npad / Cfg<L>::N);
   const int grid = (int)std::min<int64_t>(tiles, sm_count());
   if (k == 0) {  // nothing to multiply: C unchanged (beta) or zero

@@ -1,0 +1,233 @@
+// panel_coop.cuh - persistent cooperative panel factorisation (Sec. 3: the
+// unblocked partial-pivoting factorisation of one panel of width nb).
+//
+// One cooperative launch factors the whole panel rows [j0, n) x columns
+// [j0, jend): each CTA keeps a contiguous block of panel rows in shared
+// memory for all nb columns, so a column step needs no kernel launch and no
+// global-memory traffic except the pivot exchange.  Per column j:
+//   1. every CTA computes cabs1 keys of its rows i >= j and, speculatively,
+//      the reciprocal of each candidate; its best (key, row, reciprocal) goes
+//      to a global partial;                                  -> grid barrier
+//   2. every CTA reduces all partials (same winner p everywhere; ties to the
+//      lowest row), the owner of row p publishes it as the pivot row and the
+//      owner of row j publishes row j;                        -> grid barrier
+//   3. the owners swap rows j and p in shared memory, every CTA scales its
+//      rows below j by the winner's reciprocal and applies the rank-1 update
+//      to the remaining panel columns.
+// Grid barriers are counter + generation in global memory with a bounded
+// spin (clock64 budget); a timeout sets *status and every CTA returns.
+#pragma once
+
+#include "lu_kernels.cuh"
+
+namespace mclu {
+
+constexpr int COOP_T = 256;
+constexpr long long COOP_WAIT = 2000000000LL;  // ~1 s at 2 GHz
+
+struct CoopWS {
+  unsigned *bar_count;  // arrival counter
+  unsigned *bar_gen;    // generation
+  int *status;          // nonzero: a barrier timed out
+  double *prow;         // [2][2L][nb] pivot row of the current column
+  double *srow;         // [2][2L][nb] displaced row j
+};
+
+// Sense-reversal grid barrier with a bounded wait.  Returns false on timeout.
+__device__ __forceinline__ bool coop_barrier(const CoopWS &cw, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned *gen = cw.bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(cw.bar_count, 1u) == nblocks - 1) {
+      *cw.bar_count = 0;
+      __threadfence();
+      atomicAdd(cw.bar_gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > COOP_WAIT) {
+          ok = 0;
+          atomicOr(cw.status, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok && (*(volatile int *)cw.status == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Factor panel columns [j0, jend) of rows [j0, n).  CTA b owns rows
+// [j0 + b*rpc, j0 + min((b+1)*rpc, n - j0)).  Shared memory: rpc x nb x 2L.
+template <int L>
+__global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int rpc,
+                                                      int32_t *ipiv, PanelWS<L> ws, CoopWS cw) {
+  extern __shared__ double sp[];  // [row][col][2L]
+  const int tid = threadIdx.x;
+  const int nb = (int)(jend - j0);
+  const int64_t rbeg = j0 + (int64_t)blockIdx.x * rpc;
+  const int64_t rend = min(n, rbeg + rpc);
+  const int nr = (int)max((int64_t)0, rend - rbeg);
+  auto at = [&](int r, int c) -> double * { return sp + ((size_t)r * nb + c) * 2 * L; };
+  // load the owned rows
+  for (int t = tid; t < nr * nb; t += COOP_T) {
+    const int r = t % nr, c = t / nr;
+    const Z<L> z = ldz<L>(A, rbeg + r, j0 + c);
+    double *d = at(r, c);
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      d[q] = z.re.x[q];
+      d[L + q] = z.im.x[q];
+    }
+  }
+  __syncthreads();
+  __shared__ int s_p, s_zero, s_part;
+  for (int jc = 0; jc < nb; jc++) {
+    const int64_t j = j0 + jc;
+    // 1. keys and speculative reciprocals of the rows i >= j of this CTA
+    R<L> key = invalid_key<L>();
+    int idx = INT_MAX;
+    Z<L> rcp = z_zero<L>();
+    for (int r = tid; r < nr; r += COOP_T) {
+      const int64_t i = rbeg + r;
+      if (i < j) continue;
+      Z<L> a;
+      const double *d = at(r, jc);
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        a.re.x[q] = d[q];
+        a.im.x[q] = d[L + q];
+      }
+      const R<L> k = pivot_key<L>(a);
+      if (better<L>(k, (int)i, key, idx)) {
+        key = k;
+        idx = (int)i;
+        rcp = z_inv<L>(a);
+      }
+    }
+    write_partial<L>(key, idx, rcp, ws, blockIdx.x, tid, COOP_T);
+    if (!coop_barrier(cw, gridDim.x)) return;
+    // 2. reduce the partials (every CTA, same result)
+    {
+      R<L> bk = invalid_key<L>();
+      int bi = INT_MAX, bq = -1;
+      for (int q = tid; q < (int)gridDim.x; q += COOP_T) {
+        R<L> k;
+#pragma unroll
+        for (int l = 0; l < L; l++) k.x[l] = __ldcg(ws.part_key + (int64_t)q * L + l);
+        const int i = __ldcg(ws.part_idx + q);
+        if (better<L>(k, i, bk, bi)) {
+          bk = k;
+          bi = i;
+          bq = q;
+        }
+      }
+      const int my = bi;
+      block_argmax<L>(bk, bi, tid, COOP_T);
+      if (tid == 0) {
+        const bool zero = !(bk.x[0] > 0.0);
+        s_p = (bi == INT_MAX || zero) ? (int)j : bi;
+        s_zero = zero ? 1 : 0;
+      }
+      __syncthreads();
+      if (my == s_p && my != INT_MAX && !s_zero) s_part = bq;
+      __syncthreads();
+    }
+    const int64_t p = s_p;
+    const bool zero = s_zero != 0;
+    const int slot = jc & 1;
+    double *prow = cw.prow + (size_t)slot * 2 * L * nb;
+    double *srow = cw.srow + (size_t)slot * 2 * L * nb;
+    // publish the pivot row (row p) and the displaced row j
+    if (p >= rbeg && p < rend) {
+      for (int t = tid; t < nb * 2 * L; t += COOP_T) prow[t] = at((int)(p - rbeg), t / (2 * L))[t % (2 * L)];
+    }
+    if (p != j && j >= rbeg && j < rend) {
+      for (int t = tid; t < nb * 2 * L; t += COOP_T) srow[t] = at((int)(j - rbeg), t / (2 * L))[t % (2 * L)];
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+      ipiv[j] = (int32_t)(p + 1);
+      if (zero && *ws.info == 0) *ws.info = (int)(j + 1);
+    }
+    if (!coop_barrier(cw, gridDim.x)) return;
+    // 3. swap in shared memory, then scale and update
+    if (p != j) {
+      if (p >= rbeg && p < rend)
+        for (int t = tid; t < nb * 2 * L; t += COOP_T) at((int)(p - rbeg), t / (2 * L))[t % (2 * L)] = __ldcg(srow + t);
+      if (j >= rbeg && j < rend)
+        for (int t = tid; t < nb * 2 * L; t += COOP_T) at((int)(j - rbeg), t / (2 * L))[t % (2 * L)] = __ldcg(prow + t);
+    }
+    __syncthreads();
+    if (!zero) {
+      Z<L> r;
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        r.re.x[q] = __ldcg(ws.part_rcp + (int64_t)s_part * 2 * L + q);
+        r.im.x[q] = __ldcg(ws.part_rcp + (int64_t)s_part * 2 * L + L + q);
+      }
+      // multipliers of the rows below j
+      for (int rr = tid; rr < nr; rr += COOP_T) {
+        if (rbeg + rr <= j) continue;
+        double *d = at(rr, jc);
+        Z<L> a;
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          a.re.x[q] = d[q];
+          a.im.x[q] = d[L + q];
+        }
+        const Z<L> l = z_mul<L>(a, r);
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          d[q] = l.re.x[q];
+          d[L + q] = l.im.x[q];
+        }
+      }
+      __syncthreads();
+      // rank-1 update of columns jc+1 .. nb-1 (pivot row read from the global copy)
+      const int ncol = nb - jc - 1;
+      for (int t = tid; t < nr * ncol; t += COOP_T) {
+        const int rr = t % nr, cc = jc + 1 + t / nr;
+        if (rbeg + rr <= j) continue;
+        double *d = at(rr, cc);
+        const double *dl = at(rr, jc);
+        Z<L> a, l, u;
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          a.re.x[q] = d[q];
+          a.im.x[q] = d[L + q];
+          l.re.x[q] = dl[q];
+          l.im.x[q] = dl[L + q];
+          u.re.x[q] = __ldcg(prow + (size_t)cc * 2 * L + q);
+          u.im.x[q] = __ldcg(prow + (size_t)cc * 2 * L + L + q);
+        }
+        const Z<L> z = z_fms<L>(a, l, u);
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          d[q] = z.re.x[q];
+          d[L + q] = z.im.x[q];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // write the owned rows back
+  for (int t = tid; t < nr * nb; t += COOP_T) {
+    const int r = t % nr, c = t / nr;
+    const double *d = at(r, c);
+    Z<L> z;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      z.re.x[q] = d[q];
+      z.im.x[q] = d[L + q];
+    }
+    stz<L>(A, rbeg + r, j0 + c, z);
+  }
+}
+
+}  // namespace mclu
