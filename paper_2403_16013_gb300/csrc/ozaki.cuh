@@ -53,26 +53,29 @@ struct Cfg;
 // beta: digit bits; S: slices; N: realified columns per tile; FW: 32-bit words of
 // the fold accumulator F; TW: words of the split integer T; RW: words of the
 // final C - P frame; GS: diagonals pre-combined in int64 (GS diagonals of at
-// most 2^24, shifted by beta each, stay below 2^60).
+// most 2^24, shifted by beta each, stay below 2^60); EW: epilogue warps
+// (16 for DD's 32-column tiles, 8 for the 16-column TD/QD tiles: measured).
 template <>
 struct Cfg<2> {
-  static constexpr int BETA = 8, S = 14, N = 32, FW = 5, TW = 4, RW = 6, GS = 5;
+  static constexpr int BETA = 8, S = 14, N = 32, FW = 5, TW = 4, RW = 6, GS = 5, EW = 16;
 };
 template <>
 struct Cfg<3> {
-  static constexpr int BETA = 7, S = 24, N = 16, FW = 7, TW = 6, RW = 8, GS = 6;
+  static constexpr int BETA = 7, S = 24, N = 16, FW = 7, TW = 6, RW = 8, GS = 6, EW = 8;
 };
 template <>
 struct Cfg<4> {
-  static constexpr int BETA = 7, S = 32, N = 16, FW = 9, TW = 8, RW = 10, GS = 6;
+  static constexpr int BETA = 7, S = 32, N = 16, FW = 9, TW = 8, RW = 10, GS = 6, EW = 8;
 };
 
 constexpr int KC = 64;         // realified K per chunk (32 complex columns of A)
 constexpr int NB_MAX = KC / 2; // complex panel width per chunk
 constexpr int BM = 128;        // tile rows (TMEM lanes)
 constexpr int NST = 4;         // A pipeline stages
-constexpr int EPI_WARPS = 8;
-constexpr int THREADS = 32 * (2 + EPI_WARPS);
+template <int L>
+constexpr int threads_of() {
+  return 32 * (2 + Cfg<L>::EW);
+}
 constexpr int TMEM_COLS = 512;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bound on every wait
 
@@ -159,6 +162,13 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t (&r)[16]) {
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<4>(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
 }
 
 template <>
@@ -607,9 +617,9 @@ __device__ __forceinline__ void fold_diagonals(uint32_t (&F)[NH][Cfg<L>::FW], ui
 // C (m x n complex) = C - A B (BETA) or A B, from the slices of A (rows) and
 // B (columns) cut by k_oz_split_a / k_oz_split_b.  Persistent: one CTA per SM
 // walks the (row tile, column tile) grid.  Warp 0 lane 0: TMA producer.
-// Warp 1: TMEM owner and MMA issuer (lane 0).  Warps 2..9: epilogue.
+// Warp 1: TMEM owner and MMA issuer (lane 0).  Warps 2 .. 1+EW: epilogue.
 template <int L, bool BETA>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(threads_of<L>(), 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, View C, int64_t m,
               int64_t n, int nchunks, int Mpad, int Npad, const int *Ea, const int *Eb, int *status) {
   using CF = Cfg<L>;
@@ -617,7 +627,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   constexpr int A_BYTES = BM * KC * 2;  // 16 KB
   constexpr int B_TILE = N * KC * 2;    // 4 KB or 2 KB (multiples of 1024 B)
   constexpr int B_BYTES = S * B_TILE;
-  constexpr int NH = N / 2;             // columns per epilogue thread
+  constexpr int EPI_WARPS = Cfg<L>::EW;
+  constexpr int NPART = EPI_WARPS / 4;   // epilogue warps per TMEM lane quarter
+  constexpr int NH = N / NPART;          // columns per epilogue thread
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sB = base;
@@ -718,9 +730,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else {  // ---------------------------------------------------- epilogue
-    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const int quarter = warp & 3, half = (warp - 2) >> 2;  // half: column part 0 .. NPART-1
     const int row = quarter * 32 + lane;
-    const int etid = threadIdx.x - 64;  // 0 .. 255
+    const int etid = threadIdx.x - 64;  // 0 .. 32 * EPI_WARPS - 1
     const Scratch sc{reinterpret_cast<uint32_t *>(sA + NST * A_BYTES) + etid, EPI_WARPS * 32};
     const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * NH);
     uint32_t r = 0;
@@ -894,7 +906,8 @@ int gemm(bool beta, View A, View B, View C, int64_t m, int64_t n, int64_t k, voi
   rc = make_map(&tmB, w + z.a_bytes, (uint64_t)z.nchunks * Cfg<L>::S * z.Npad, Cfg<L>::N);
   if (rc) return rc;
   constexpr int A_BYTES = BM * KC * 2, B_BYTES = Cfg<L>::S * Cfg<L>::N * KC * 2;
-  constexpr int SCR_BYTES = (2 * Cfg<L>::RW + 2) * EPI_WARPS * 32 * 4;  // epilogue scratch
+  constexpr int SCR_BYTES = (2 * Cfg<L>::RW + 2) * Cfg<L>::EW * 32 * 4;  // epilogue scratch
+  constexpr int THREADS = threads_of<L>();
   // at least ~116 KB so that a single CTA (and its 512 TMEM columns) fits per SM
   const int smem = std::max(B_BYTES + NST * A_BYTES + SCR_BYTES + 1024, 116 * 1024);
   const int64_t tiles = ((m + BM - 1) / BM) * (z.Npad / Cfg<L>::N);
