@@ -7,6 +7,11 @@ leading limbs, canonical lower limbs, seed 1), i.e. one pass over the whole
 hot path.  value = steps * 8 n^3 / 3 / elapsed, summed over ranks (each rank
 an independent replica; the path has no data exchange).
 
+The default step uses the Ozaki-scheme trailing update on the tensor cores
+(nb = 32); the same step with the plain FP64-pipe 4M update (nb = 64) is
+timed right after it and reported under "plain", with both backward errors,
+so that the speed-up is stated at equal accuracy.
+
 Timing: W untimed warm-up steps, then K steps between a barrier +
 torch.cuda.synchronize() on both sides, CUDA events on the library's stream,
 max over ranks.  The matrix (537 MB in DD) is larger than L2 (129 MB), so no
@@ -44,6 +49,8 @@ LIMBS = {"dd": 2, "td": 3, "qd": 4}
 FP64_OPS_PEAK = 0.625e12
 # Ozaki-scheme engine: slices S per precision; kept pairs p + q <= S - 1.
 OZAKI_S = {"dd": 14, "td": 24, "qd": 32}
+# unit roundoff exponents: u = 2^-104 / 2^-157 / 2^-209
+U_EXP = {"dd": 104, "td": 157, "qd": 209}
 
 
 def measured_bf16_peak() -> tuple[float, str]:
@@ -62,10 +69,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="mclu", choices=["mclu", "reference"])
     p.add_argument("--prec", default="dd", choices=["dd", "td", "qd"])
-    p.add_argument("--method", default="4m", choices=["4m", "3m", "unblocked", "ozaki"])
+    p.add_argument("--method", default="ozaki", choices=["4m", "3m", "unblocked", "ozaki"])
     p.add_argument("--n", type=int, default=4096)
     p.add_argument("--nb", type=int, default=0, help="panel width (0: 64, or 32 for ozaki)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-plain", action="store_true", help="skip the plain 4M comparison of an ozaki run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle sample")
     return p.parse_args()
@@ -216,6 +224,72 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el_ms: float):
+    """Roofline of the dominant kernel, the trailing update: algorithmic work per
+    launch (from n, nb and the method) over its average event-timed duration."""
+    L = LIMBS[prec]
+    gemm_ms, gemm_calls = prof["gemm"]
+    if not gemm_calls:
+        return None
+    if method == "ozaki":
+        S = OZAKI_S[prec]
+        pairs = S * (S + 1) // 2
+        # realified real GEMM per kept slice pair: n2 x (2 n2) x (2 jb), 2 flops per MAC
+        flops = 0.0
+        for j0 in range(0, n, nb):
+            jb = min(nb, n - j0)
+            n2 = n - j0 - jb
+            flops += pairs * 2.0 * n2 * (2 * n2) * (2 * jb)
+        per_launch = flops / (gemm_calls / steps)
+        achieved = per_launch / (gemm_ms / gemm_calls * 1e-3) / 1e12
+        peak, src = measured_bf16_peak()
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": src + " bf16 burst", "traffic": None,
+                "kernel": f"k_oz_gemm<{L},beta> (+ split kernels, counted in its time)",
+                "flops_per_launch": per_launch, "avg_launch_ms": gemm_ms / gemm_calls,
+                "share_of_step": gemm_ms / el_ms}
+    if method in ("4m", "3m"):
+        macs = 0
+        for j0 in range(0, n, nb):
+            jb = min(nb, n - j0)
+            n2 = n - j0 - jb
+            macs += n2 * n2 * jb
+        per_mac = (3 if method == "3m" else 4) * I_REAL[prec]
+        per_launch_ops = macs * per_mac / (gemm_calls / steps)
+        achieved = per_launch_ops / (gemm_ms / gemm_calls * 1e-3)
+        return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "T FP64-ops/s",
+                "frac": achieved / FP64_OPS_PEAK, "peak_source": "nominal FP64 (1.25 TFLOP/s, FMA = 2)",
+                "traffic": None, "kernel": f"k_gemm<{L},{'3M' if method == '3m' else '4M'},beta>",
+                "ops_per_launch": per_launch_ops, "avg_launch_ms": gemm_ms / gemm_calls,
+                "share_of_step": gemm_ms / el_ms}
+    return None
+
+
+def backward_error(api, A0, X, B0):
+    """||b - A x||_inf / (||A||_inf ||x||_inf) (modulus norms).  The residual is
+    formed by the library's QD ZGEMM on the limbs zero-padded to four, which
+    resolves it far below the bound for DD and TD.  A QD residual lies below
+    the resolution of a four-limb accumulation, so for QD None is returned
+    (the tests check it with the exact residual)."""
+    import torch
+    L = A0.shape[1]
+    if L == 4:
+        return None
+
+    def pad(T):
+        if L == 4:
+            return T
+        P = torch.zeros((2, 4) + tuple(T.shape[2:]), dtype=T.dtype, device=T.device)
+        P[:, :L] = T
+        return P
+
+    R = api.zgemm(pad(A0), pad(X), C=pad(B0))
+    r = torch.hypot(R[0, 0], R[1, 0]).max().item()
+    anorm = torch.hypot(A0[0, 0], A0[1, 0]).sum(dim=0).max().item()
+    xnorm = torch.hypot(X[0, 0], X[1, 0]).max().item()
+    return r / (anorm * xnorm)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -229,8 +303,7 @@ def main():
     build.build()
     binding.load()
     n, L, prec = args.n, LIMBS[args.prec], args.prec
-    if args.nb == 0:
-        args.nb = 32 if args.method == "ozaki" else 64
+    nb_of = lambda m: args.nb if args.nb else (32 if m == "ozaki" else 64)
     A_h, b_h = make_inputs(n, L)
     A0 = torch.from_numpy(A_h).cuda()
     b0 = torch.from_numpy(b_h).cuda()
@@ -239,87 +312,69 @@ def main():
     ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
-    method = args.method
-
-    def step():
-        A.copy_(A0)
-        api.lu_factor_(A, ipiv, info, method=method, nb=args.nb)
-        x.copy_(b0)
-        api.lu_solve(A, ipiv, x, inplace=True)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if int(info.item()) != 0:
-        raise RuntimeError("singular benchmark matrix")
-
-    sampler = ClockSampler(local)
-    barrier(ws)
-    torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.4)
-    binding.profile_begin(("gemm", "panel", "trsm", "laswp", "getrs", "other"))
-    launches0 = binding.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(ws)
-    launches = binding.launch_count() - launches0
-    prof = binding.profile_end()
-    clocks = sampler.stop()
-    el_ms = max_over_ranks(e0.elapsed_time(e1), ws)
     flops = 8.0 * n ** 3 / 3.0
-    value = job_throughput(ws, args.steps, flops, el_ms)
 
-    # roofline of the dominant kernel: the trailing-update GEMM on the FP64 pipe
-    nb = args.nb
-    macs = 0
-    for j0 in range(0, n, nb):
-        jb = min(nb, n - j0)
-        n2 = n - j0 - jb
-        macs += n2 * n2 * jb
-    per_mac = (3 if method == "3m" else 4) * I_REAL[prec]
-    gemm_ms, gemm_calls = prof["gemm"]
-    roof = None
-    if gemm_calls and method == "ozaki":
-        S = OZAKI_S[prec]
-        pairs = S * (S + 1) // 2
-        # realified real GEMM per pair: (m) x (2 n2) x (2 jb), 2 flops per MAC
-        flops = 0
-        for j0 in range(0, n, nb):
-            jb = min(nb, n - j0)
-            n2 = n - j0 - jb
-            flops += pairs * 2.0 * n2 * (2 * n2) * (2 * jb)
-        per_launch = flops / (gemm_calls / args.steps)
-        achieved = per_launch / (gemm_ms / gemm_calls * 1e-3) / 1e12
-        peak, src = measured_bf16_peak()
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": src, "traffic": None,
-                "kernel": f"k_oz_gemm<{L},beta> (+ split kernels, counted in its time)",
-                "flops_per_launch": per_launch, "avg_launch_ms": gemm_ms / gemm_calls,
-                "share_of_step": gemm_ms / el_ms}
-    if gemm_calls and method in ("4m", "3m"):
-        per_launch_ops = macs * per_mac / (gemm_calls / args.steps)
-        achieved = per_launch_ops / (gemm_ms / gemm_calls * 1e-3)
-        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "T FP64-ops/s",
-                "frac": achieved / FP64_OPS_PEAK, "traffic": None,
-                "kernel": f"k_gemm<{L},{'3M' if method == '3m' else '4M'},beta>",
-                "ops_per_launch": per_launch_ops, "avg_launch_ms": gemm_ms / gemm_calls,
-                "share_of_step": gemm_ms / el_ms}
+    def timed(method: str, nb: int, sampler=None) -> dict:
+        def step():
+            A.copy_(A0)
+            api.lu_factor_(A, ipiv, info, method=method, nb=nb)
+            x.copy_(b0)
+            api.lu_solve(A, ipiv, x, inplace=True)
 
-    line = {"metric": "complex DD/TD/QD LU GFLOPS (8n^3/3/t) at n=4096", "value": value, "unit": "GFLOP/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if int(info.item()) != 0:
+            raise RuntimeError(f"zgetrf info {int(info.item())} on the benchmark matrix")
+        barrier(ws)
+        torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.start()
+            time.sleep(0.4)
+        binding.profile_begin(("gemm", "panel", "trsm", "laswp", "getrs", "other"))
+        launches0 = binding.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        launches = binding.launch_count() - launches0
+        prof = binding.profile_end()
+        clocks = sampler.stop() if sampler is not None else None
+        el_ms = max_over_ranks(e0.elapsed_time(e1), ws)
+        return {"el_ms": el_ms, "launches": launches, "prof": prof, "clocks": clocks,
+                "value": job_throughput(ws, args.steps, flops, el_ms),
+                "backward_error": backward_error(api, A0, x, b0),
+                "roofline": roofline(method, prec, n, nb, args.steps, prof, el_ms)}
+
+    method, nb = args.method, nb_of(args.method)
+    main_run = timed(method, nb, ClockSampler(local))
+    bound = 16.0 * n * 2.0 ** -U_EXP[prec]
+    line = {"metric": "complex DD/TD/QD LU GFLOPS (8n^3/3/t) at n=4096", "value": main_run["value"],
+            "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": main_run["el_ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"complex {prec.upper()} LU (zgetrf, partial pivoting) + solve (zgetrs), n={n}, "
                                    f"nb={nb}, {method.upper()} trailing update, Gaussian limbs seed 1",
                        "n": n, "prec": prec, "method": method, "nb": nb,
                        "l2": "inputs larger than L2 (%.0f MB per matrix), no flush" % (A_h.nbytes / 1e6),
                        "parallelism": f"replicas x{ws}"},
-            "gpu_launches": launches, "clocks": clocks, "roofline": roof,
-            "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+            "gpu_launches": main_run["launches"], "clocks": main_run["clocks"], "roofline": main_run["roofline"],
+            "phases_ms_per_step": {k: v[0] / args.steps for k, v in main_run["prof"].items()},
+            "accuracy": {"backward_error": main_run["backward_error"], "bound_16nu": bound,
+                         "residual": "b - A x by the library's QD ZGEMM" if L < 4 else
+                         "not resolvable in four limbs; exact check in the tests"}}
+
+    if method == "ozaki" and not args.no_plain:
+        # the same step with the plain FP64-pipe 4M update, for the speed-up at equal accuracy
+        plain = timed("4m", args.nb if args.nb else 64)
+        line["plain"] = {"method": "4m", "nb": args.nb if args.nb else 64, "value": plain["value"],
+                         "unit": "GFLOP/s", "ms_per_step": plain["el_ms"] / args.steps,
+                         "backward_error": plain["backward_error"], "roofline": plain["roofline"],
+                         "phases_ms_per_step": {k: v[0] / args.steps for k, v in plain["prof"].items()}}
+        line["ozaki_speedup_vs_plain"] = main_run["value"] / plain["value"]
 
     if not args.no_e2e:
         A_pin = torch.from_numpy(A_h).pin_memory()
@@ -329,7 +384,7 @@ def main():
 
         def e2e_step():
             A.copy_(A_pin, non_blocking=True)
-            api.lu_factor_(A, ipiv, info, method=method, nb=args.nb)
+            api.lu_factor_(A, ipiv, info, method=method, nb=nb)
             x.copy_(b_pin, non_blocking=True)
             api.lu_solve(A, ipiv, x, inplace=True)
             x_pin.copy_(x, non_blocking=True)

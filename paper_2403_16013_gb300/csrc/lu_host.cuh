@@ -334,31 +334,33 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   return 0;
 }
 
-// Forward (LOWER) or backward substitution over all diagonal blocks of T on
-// the n x nrhs planes X.
-// rdiag: reciprocals of the diagonal (planes [2L][n]) when !UNIT.
-template <int L, bool LOWER, bool UNIT, bool CONJT>
-int tri_solve(View A, int64_t n, View X, int64_t nrhs, const double *rdiag, cudaStream_t s) {
-  constexpr int BS = 32;
+// Forward (LOWER) or backward substitution with op(T) over all diagonal
+// blocks: R holds the right-hand sides on entry and is consumed as the
+// residual; the solution goes to Y.  W: inverses of the diagonal blocks of
+// T (k_blk_inv), applied as their conjugate transposes with CONJT.
+template <int L, bool LOWER, bool CONJT>
+int tri_solve(View A, int64_t n, const double *W, View R, View Y, int64_t nrhs, cudaStream_t s) {
+  constexpr int BS = SOLVE_BS;
+  constexpr size_t smem = blk_solve_smem<L>();
+  if (smem > 48 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      MCLU_TRY(cudaFuncSetAttribute(k_blk_solve<L, LOWER, CONJT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      attr = true;
+    }
+  }
   const int64_t nblk = cdiv(n, BS);
-  const int CT = nrhs >= 8 ? 8 : (int)nrhs;
-  for (int64_t q = 0; q < nblk; q++) {
-    const int64_t b = LOWER ? q : nblk - 1 - q;
-    const int64_t k0 = b * BS;
-    const int bs = (int)std::min<int64_t>(BS, n - k0);
-    int rc = launch_tri_block<L, LOWER, UNIT, CONJT>(dim3((unsigned)cdiv(nrhs, CT)), dim3(BS, CT), s, A, k0, bs, X,
-                                                     nrhs, rdiag, n, k0);
-    if (rc) return rc;
-    const int64_t r0 = LOWER ? k0 + bs : 0, r1 = LOWER ? n : k0;
-    if (r1 > r0) {
-      dim3 grid((unsigned)cdiv(r1 - r0, 32), (unsigned)nrhs);
-      static bool attr = false;
-      if (!attr) {
-        MCLU_TRY(cudaFuncSetAttribute(k_gemv<L, CONJT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)gemv_smem<L>()));
-        attr = true;
-      }
-      k_gemv<L, CONJT><<<grid, 256, gemv_smem<L>(), s>>>(A, r0, r1, k0, bs, X, nrhs);
+  for (int64_t c0 = 0; c0 < nrhs; c0 += 65535) {
+    const int64_t nc = std::min<int64_t>(65535, nrhs - c0);
+    const View Rc{R.p + c0 * R.ld, R.ld, R.ps}, Yc{Y.p + c0 * Y.ld, Y.ld, Y.ps};
+    for (int64_t q = 0; q < nblk; q++) {
+      const int64_t b = LOWER ? q : nblk - 1 - q;
+      const int64_t k0 = b * BS;
+      const int bs = (int)std::min<int64_t>(BS, n - k0);
+      const int64_t r0 = LOWER ? k0 + bs : 0, r1 = LOWER ? n : k0;
+      const dim3 grid((unsigned)std::max<int64_t>(1, cdiv(r1 - r0, 32)), (unsigned)nc);
+      k_blk_solve<L, LOWER, CONJT><<<grid, 256, smem, s>>>(A, k0, bs, W + b * 2 * L * BS * BS, Rc, Yc, r0, r1);
       MCLU_LAUNCHED();
     }
   }
@@ -382,17 +384,31 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
   ProfScope ps(PK_SOLVE, s);
   View A{const_cast<double *>(Ap), lda, lda * n};
   View B{Bp, ldb, ldb * nrhs};
+  constexpr int BS = SOLVE_BS;
+  const int64_t nblk = cdiv(n, BS);
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t perm_bytes = al((size_t)n * sizeof(int32_t));
+  const size_t rdiag_bytes = al((size_t)2 * L * n * sizeof(double));
+  const size_t inv_bytes = al((size_t)nblk * 2 * L * BS * BS * sizeof(double));
+  const size_t vec_bytes = al((size_t)2 * L * n * nrhs * sizeof(double));
   Workspace w;
-  const size_t perm_bytes = ((size_t)n * sizeof(int32_t) + 255) & ~(size_t)255;
-  const size_t rdiag_bytes = ((size_t)2 * L * n * sizeof(double) + 255) & ~(size_t)255;
-  MCLU_TRY(w.alloc(perm_bytes + rdiag_bytes + (size_t)2 * L * n * nrhs * sizeof(double), s));
-  int32_t *perm = (int32_t *)w.p;
-  double *rdiag = (double *)((char *)w.p + perm_bytes);
-  View X{(double *)((char *)w.p + perm_bytes + rdiag_bytes), n, n * nrhs};
-  if (!conj)
-    k_diag_recip<L, false><<<(unsigned)cdiv(n, 128), 128, 0, s>>>(A, n, rdiag, n);
-  else
-    k_diag_recip<L, true><<<(unsigned)cdiv(n, 128), 128, 0, s>>>(A, n, rdiag, n);
+  MCLU_TRY(w.alloc(perm_bytes + rdiag_bytes + 2 * inv_bytes + 2 * vec_bytes, s));
+  char *cur = (char *)w.p;
+  int32_t *perm = (int32_t *)cur;
+  cur += perm_bytes;
+  double *rdiag = (double *)cur;
+  cur += rdiag_bytes;
+  double *WL = (double *)cur;
+  cur += inv_bytes;
+  double *WU = (double *)cur;
+  cur += inv_bytes;
+  View X{(double *)cur, n, n * nrhs};
+  cur += vec_bytes;
+  View Y{(double *)cur, n, n * nrhs};
+  // diagonal reciprocals, then the inverses of all diagonal blocks of L and U
+  k_diag_recip<L><<<(unsigned)cdiv(n, 128), 128, 0, s>>>(A, n, rdiag, n);
+  MCLU_LAUNCHED();
+  k_blk_inv<L><<<dim3((unsigned)nblk, 2), BS, 0, s>>>(A, n, WL, WU, rdiag, n);
   MCLU_LAUNCHED();
   const size_t smem_perm = (size_t)n * sizeof(int32_t);
   const int use_smem = smem_perm <= 200 * 1024 ? 1 : 0;
@@ -403,20 +419,20 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
   if (!conj) {
     k_permute<L><<<pg, 256, 0, s>>>(B, X, perm, n, nrhs, 0);  // X = P B
     MCLU_LAUNCHED();
-    int rc = tri_solve<L, true, true, false>(A, n, X, nrhs, nullptr, s);
+    int rc = tri_solve<L, true, false>(A, n, WL, X, Y, nrhs, s);  // L y = P b
     if (rc) return rc;
-    rc = tri_solve<L, false, false, false>(A, n, X, nrhs, rdiag, s);
+    rc = tri_solve<L, false, false>(A, n, WU, Y, X, nrhs, s);  // U x = y
     if (rc) return rc;
     MCLU_TRY(cudaMemcpy2DAsync(Bp, ldb * sizeof(double), X.p, n * sizeof(double), n * sizeof(double),
                                (size_t)2 * L * nrhs, cudaMemcpyDeviceToDevice, s));
   } else {
     MCLU_TRY(cudaMemcpy2DAsync(X.p, n * sizeof(double), Bp, ldb * sizeof(double), n * sizeof(double),
                                (size_t)2 * L * nrhs, cudaMemcpyDeviceToDevice, s));
-    int rc = tri_solve<L, true, false, true>(A, n, X, nrhs, rdiag, s);  // U^H w = b
+    int rc = tri_solve<L, true, true>(A, n, WU, X, Y, nrhs, s);  // U^H w = b
     if (rc) return rc;
-    rc = tri_solve<L, false, true, true>(A, n, X, nrhs, nullptr, s);    // L^H z = w
+    rc = tri_solve<L, false, true>(A, n, WL, Y, X, nrhs, s);  // L^H z = w
     if (rc) return rc;
-    k_permute<L><<<pg, 256, 0, s>>>(X, B, perm, n, nrhs, 1);     // B = P^T z
+    k_permute<L><<<pg, 256, 0, s>>>(X, B, perm, n, nrhs, 1);  // B = P^T z
     MCLU_LAUNCHED();
   }
   return 0;

@@ -451,14 +451,12 @@ __global__ void k_identity(View X, int64_t n) {
   stz<L>(X, i, j, z);
 }
 
-// rdiag[k] = 1 / T_kk for the diagonal of A (CONJT: of A^H), planes [2L][ld].
-template <int L, bool CONJT>
+// rdiag[k] = 1 / A_kk for the diagonal of A, planes [2L][ld].
+template <int L>
 __global__ void k_diag_recip(View A, int64_t n, double *rdiag, int64_t ld) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  Z<L> d = ldz<L>(A, k, k);
-  if (CONJT) d = z_conj<L>(d);
-  const Z<L> r = z_inv<L>(d);
+  const Z<L> r = z_inv<L>(ldz<L>(A, k, k));
 #pragma unroll
   for (int q = 0; q < L; q++) {
     rdiag[(int64_t)q * ld + k] = r.re.x[q];
@@ -466,74 +464,222 @@ __global__ void k_diag_recip(View A, int64_t n, double *rdiag, int64_t ld) {
   }
 }
 
-// X[r, c] -= sum_{k < bs} T(r, k0+k) X[k0+k, c] for rows r in [r0, r1), where
-// T(r, k) = A(r, k), or conj(A(k, r)) with CONJT.  Eight lanes share a row:
-// lane g accumulates the products k = g, g+8, ... on the leveled accumulator
-// (short dependent chains), the eight partial accumulators are combined level
-// by level through warp shuffles, and lane 0 adds X[r, c] and renormalises.
-// The A tile (bs x 32 rows) and the X block are staged in shared memory; with
-// CONJT the A tile is read along its columns (contiguous in memory).
+// ------------------------------------------------ blocked substitution (Sec. 4)
+//
+// The forward and back substitutions run over SOLVE_BS x SOLVE_BS diagonal
+// blocks.  The inverses of all diagonal blocks are formed first, in parallel
+// (k_blk_inv); each block step is then one launch (k_blk_solve) that applies
+// the block's inverse to the current residual of the block and subtracts the
+// block's contribution from the remaining rows.
+constexpr int SOLVE_BS = 16;
+
+// acc_re + i acc_im -= a b (complex, on the leveled accumulators)
 template <int L>
-constexpr size_t gemv_smem() {
-  return (size_t)32 * (32 + 1) * 2 * L * sizeof(double);
+__device__ __forceinline__ void acc_csub(Acc<L> &re, Acc<L> &im, const Z<L> &a, const Z<L> &b) {
+  re.template add_prod<true>(a.re, b.re);
+  re.template add_prod<false>(a.im, b.im);
+  im.template add_prod<true>(a.re, b.im);
+  im.template add_prod<true>(a.im, b.re);
 }
 
-template <int L, bool CONJT>
-__global__ void __launch_bounds__(256) k_gemv(View A, int64_t r0, int64_t r1, int64_t k0, int bs, View X,
-                                              int64_t ncols) {
-  constexpr int TR = 32, G = 8, BSM = 32;
-  extern __shared__ double gsm[];  // sA [BSM][TR][2L], then sX [BSM][2L]
-  double(*sA)[TR][2 * L] = reinterpret_cast<double(*)[TR][2 * L]>(gsm);
-  double(*sX)[2 * L] = reinterpret_cast<double(*)[2 * L]>(gsm + (size_t)BSM * TR * 2 * L);
-  const int tid = threadIdx.x;
-  const int g = tid & (G - 1), rloc = tid >> 3;  // 8 lanes per row, 32 rows per CTA
-  const int64_t r = r0 + (int64_t)blockIdx.x * TR + rloc;
-  const int64_t c = blockIdx.y;
-  for (int t = tid; t < bs * TR; t += 256) {
-    int kq, rq;
-    if (CONJT) {
-      kq = t % bs;
-      rq = t / bs;
-    } else {
-      rq = t % TR;
-      kq = t / TR;
-    }
-    const int64_t gr = r0 + (int64_t)blockIdx.x * TR + rq, gk = k0 + kq;
-    Z<L> v = z_zero<L>();
-    if (gr < r1) v = CONJT ? z_conj<L>(ldz<L>(A, gk, gr)) : ldz<L>(A, gr, gk);
+// acc_re + i acc_im += a b
+template <int L>
+__device__ __forceinline__ void acc_cadd(Acc<L> &re, Acc<L> &im, const Z<L> &a, const Z<L> &b) {
+  re.template add_prod<false>(a.re, b.re);
+  re.template add_prod<true>(a.im, b.im);
+  im.template add_prod<false>(a.re, b.im);
+  im.template add_prod<false>(a.im, b.re);
+}
+
+template <int L>
+__device__ __forceinline__ Z<L> lds_z(const double *p) {
+  Z<L> z;
 #pragma unroll
-    for (int q = 0; q < L; q++) {
-      sA[kq][rq][q] = v.re.x[q];
-      sA[kq][rq][L + q] = v.im.x[q];
-    }
+  for (int q = 0; q < L; q++) {
+    z.re.x[q] = p[q];
+    z.im.x[q] = p[L + q];
   }
-  for (int t = tid; t < bs; t += 256) {
-    Z<L> v = ldz<L>(X, k0 + t, c);
+  return z;
+}
+
+template <int L>
+__device__ __forceinline__ void sts_z(double *p, const Z<L> &z) {
 #pragma unroll
-    for (int q = 0; q < L; q++) {
-      sX[t][q] = v.re.x[q];
-      sX[t][L + q] = v.im.x[q];
+  for (int q = 0; q < L; q++) {
+    p[q] = z.re.x[q];
+    p[L + q] = z.im.x[q];
+  }
+}
+
+// Inverses of the diagonal blocks of the factors held in A: blockIdx.y = 0
+// gives inv(L_kk) of the unit lower triangle, blockIdx.y = 1 inv(U_kk) of the
+// upper triangle, whose diagonal reciprocals are rdiag (planes [2L][rld]).
+// Thread c forms column c of the inverse by substitution, each entry one
+// leveled accumulation: lower, x_i = -sum_{c <= j < i} L_ij x_j with x_c = 1;
+// upper, x_i = -(sum_{i < j <= c} U_ij x_j) / U_ii with x_c = 1 / U_cc.
+// Output W[block][2L][SOLVE_BS][SOLVE_BS], row-major (i, j), zero outside the
+// block's bs x bs extent and outside the triangle.
+template <int L>
+__global__ void __launch_bounds__(SOLVE_BS) k_blk_inv(View A, int64_t n, double *WL, double *WU, const double *rdiag,
+                                                      int64_t rld) {
+  constexpr int BS = SOLVE_BS;
+  __shared__ double sT[BS][BS][2 * L];  // T(i, j) of the diagonal block
+  __shared__ double sX[BS][BS][2 * L];  // sX[i][c]: entry (i, c) of the inverse
+  const int c = threadIdx.x;
+  const int64_t blk = blockIdx.x, k0 = blk * BS;
+  const int bs = (int)min((int64_t)BS, n - k0);
+  const bool upper = blockIdx.y == 1;
+  for (int t = c; t < BS * BS; t += BS) {
+    const int i = t % BS, j = t / BS;
+    Z<L> v = z_zero<L>();
+    if (i < bs && j < bs && (upper ? i <= j : i > j)) v = ldz<L>(A, k0 + i, k0 + j);
+    sts_z<L>(sT[i][j], v);
+    sts_z<L>(sX[i][j], z_zero<L>());
+  }
+  __syncthreads();
+  if (c < bs) {
+    if (!upper) {
+      Z<L> one = z_zero<L>();
+      one.re.x[0] = 1.0;
+      sts_z<L>(sX[c][c], one);
+      for (int i = c + 1; i < bs; i++) {
+        Acc<L> re, im;
+        re.zero();
+        im.zero();
+        for (int j = c; j < i; j++) acc_csub<L>(re, im, lds_z<L>(sT[i][j]), lds_z<L>(sX[j][c]));
+        Z<L> x;
+        x.re = re.result();
+        x.im = im.result();
+        sts_z<L>(sX[i][c], x);
+      }
+    } else {
+      auto recip = [&](int i) {
+        Z<L> r;
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          r.re.x[q] = rdiag[(int64_t)q * rld + k0 + i];
+          r.im.x[q] = rdiag[(int64_t)(L + q) * rld + k0 + i];
+        }
+        return r;
+      };
+      sts_z<L>(sX[c][c], recip(c));
+      for (int i = c - 1; i >= 0; i--) {
+        Acc<L> re, im;
+        re.zero();
+        im.zero();
+        for (int j = i + 1; j <= c; j++) acc_csub<L>(re, im, lds_z<L>(sT[i][j]), lds_z<L>(sX[j][c]));
+        Z<L> x;
+        x.re = re.result();
+        x.im = im.result();
+        sts_z<L>(sX[i][c], z_mul<L>(x, recip(i)));
+      }
     }
   }
   __syncthreads();
+  double *W = (upper ? WU : WL) + blk * 2 * L * BS * BS;
+  for (int i = 0; i < BS; i++)
+#pragma unroll
+    for (int q = 0; q < 2 * L; q++) W[((size_t)q * BS + i) * BS + c] = sX[i][c][q];
+}
+
+// Shared memory of k_blk_solve: A tile [SOLVE_BS][32][2L], op(W) [SOLVE_BS][SOLVE_BS][2L],
+// r_k and x_k [SOLVE_BS][2L] each.
+template <int L>
+constexpr size_t blk_solve_smem() {
+  return ((size_t)SOLVE_BS * 32 + SOLVE_BS * SOLVE_BS + 2 * SOLVE_BS) * 2 * L * sizeof(double);
+}
+
+// One step of the blocked substitution for the diagonal block at k0 (bs <=
+// SOLVE_BS rows) on column blockIdx.y of the residual R:
+//   1. x_k = op(Wk) r_k, Wk the block's inverse (op: identity, or the
+//      conjugate transpose with CONJT).  Four lanes share a row of Wk, only
+//      the triangle is visited, and the partial accumulators are combined
+//      through warp shuffles.  Every CTA forms x_k (a 16 x 16 product); the
+//      CTAs with blockIdx.x = 0 store it in Y.
+//   2. R[r] -= sum_j op(T)(r, k0+j) x_j for the rows r in [r0, r1), where
+//      op(T)(r, j) = A(r, j), or conj(A(j, r)) with CONJT.  Eight lanes share a
+//      row, 32 rows per CTA; the A tile is staged in shared memory (read along
+//      its columns with CONJT, contiguous in memory).
+// No CTA writes rows of block k of R, so every CTA reads the same r_k.
+template <int L, bool LOWER, bool CONJT>
+__global__ void __launch_bounds__(256) k_blk_solve(View A, int64_t k0, int bs, const double *Wk, View R, View Y,
+                                                   int64_t r0, int64_t r1) {
+  constexpr int BS = SOLVE_BS, TR = 32, G = 8, G1 = 4;
+  extern __shared__ double bsm[];
+  double(*sA)[TR][2 * L] = reinterpret_cast<double(*)[TR][2 * L]>(bsm);
+  double(*sW)[BS][2 * L] = reinterpret_cast<double(*)[BS][2 * L]>(bsm + (size_t)BS * TR * 2 * L);
+  double(*sR)[2 * L] = reinterpret_cast<double(*)[2 * L]>(bsm + ((size_t)BS * TR + BS * BS) * 2 * L);
+  double(*sX)[2 * L] = sR + BS;
+  const int tid = threadIdx.x;
+  const int64_t c = blockIdx.y;
+  const int64_t rbase = r0 + (int64_t)blockIdx.x * TR;
+  // stage op(Wk), r_k and the A tile
+  for (int t = tid; t < BS * BS * 2 * L; t += 256) {
+    const int q = t / (BS * BS), ij = t % (BS * BS);
+    const int i = ij / BS, j = ij % BS;
+    double v;
+    if (CONJT) {
+      v = Wk[((size_t)q * BS + j) * BS + i];
+      if (q >= L) v = -v;
+    } else {
+      v = Wk[((size_t)q * BS + i) * BS + j];
+    }
+    sW[i][j][q] = v;
+  }
+  for (int t = tid; t < BS; t += 256) sts_z<L>(sR[t], t < bs ? ldz<L>(R, k0 + t, c) : z_zero<L>());
+  if (r1 > r0) {
+    for (int t = tid; t < bs * TR; t += 256) {
+      int kq, rq;
+      if (CONJT) {
+        kq = t % bs;
+        rq = t / bs;
+      } else {
+        rq = t % TR;
+        kq = t / TR;
+      }
+      const int64_t gr = rbase + rq, gk = k0 + kq;
+      Z<L> v = z_zero<L>();
+      if (gr < r1) v = CONJT ? z_conj<L>(ldz<L>(A, gk, gr)) : ldz<L>(A, gr, gk);
+      sts_z<L>(sA[kq][rq], v);
+    }
+  }
+  __syncthreads();
+  // 1. x_k = op(Wk) r_k on the first BS * G1 threads (whole warps)
+  if (tid < BS * G1) {
+    const int i = tid / G1, g = tid % G1;
+    Acc<L> re, im;
+    re.zero();
+    im.zero();
+    const int jlo = LOWER ? 0 : i, jhi = LOWER ? i : bs - 1;
+    for (int j = jlo + g; j <= jhi && j < bs; j += G1) acc_cadd<L>(re, im, lds_z<L>(sW[i][j]), lds_z<L>(sR[j]));
+#pragma unroll
+    for (int off = G1 / 2; off > 0; off >>= 1) {
+      Acc<L> ore, oim;
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        ore.s[q] = __shfl_down_sync(0xffffffffu, re.s[q], off, G1);
+        oim.s[q] = __shfl_down_sync(0xffffffffu, im.s[q], off, G1);
+      }
+      re.add_acc(ore, false);
+      im.add_acc(oim, false);
+    }
+    if (g == 0) {
+      Z<L> x;
+      x.re = re.result();
+      x.im = im.result();
+      sts_z<L>(sX[i], x);
+      if (blockIdx.x == 0 && i < bs) stz<L>(Y, k0 + i, c, x);
+    }
+  }
+  __syncthreads();
+  if (r1 <= r0) return;
+  // 2. the remaining rows lose the block's contribution
+  const int g = tid & (G - 1), rloc = tid >> 3;
+  const int64_t r = rbase + rloc;
   Acc<L> are, aim;
   are.zero();
   aim.zero();
-  for (int kq = g; kq < bs; kq += G) {
-    R<L> ar, ai, xr, xi;
-#pragma unroll
-    for (int q = 0; q < L; q++) {
-      ar.x[q] = sA[kq][rloc][q];
-      ai.x[q] = sA[kq][rloc][L + q];
-      xr.x[q] = sX[kq][q];
-      xi.x[q] = sX[kq][L + q];
-    }
-    are.template add_prod<true>(ar, xr);
-    are.template add_prod<false>(ai, xi);
-    aim.template add_prod<true>(ar, xi);
-    aim.template add_prod<true>(ai, xr);
-  }
-  // combine the 8 partial accumulators of this row (lanes g = 0..7)
+  for (int kq = g; kq < bs; kq += G) acc_csub<L>(are, aim, lds_z<L>(sA[kq][rloc]), lds_z<L>(sX[kq]));
 #pragma unroll
   for (int off = G / 2; off > 0; off >>= 1) {
     Acc<L> ore, oim;
@@ -546,13 +692,13 @@ __global__ void __launch_bounds__(256) k_gemv(View A, int64_t r0, int64_t r1, in
     aim.add_acc(oim, false);
   }
   if (g == 0 && r < r1) {
-    const Z<L> x0 = ldz<L>(X, r, c);
+    const Z<L> x0 = ldz<L>(R, r, c);
     are.add(x0.re);
     aim.add(x0.im);
     Z<L> z;
     z.re = are.result();
     z.im = aim.result();
-    stz<L>(X, r, c, z);
+    stz<L>(R, r, c, z);
   }
 }
 
