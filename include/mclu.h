@@ -95,7 +95,7 @@ int zgetrf_qd_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info
  * that may not allocate device memory during the call (inside a CUDA graph
  * capture, real-time code that allows no allocator calls after start-up, or
  * a host that gives the library only its own buffers).  Its scratch is one
- * fixed device array in the library (about 540 KB, held on every GPU that
+ * fixed device array in the library (about 1.6 MB, held on every GPU that
  * loads the library until the process exits), so:
  *   n     0 <= n <= zgetrf_dd_noalloc_max_n() (8192); larger n returns
  *         MCLU_ERR_SCRATCH_CAPACITY and enqueues nothing

@@ -83,15 +83,30 @@ struct Carver {  // 256-byte aligned sub-allocations of one workspace block
   }
 };
 
+// Pivot-partial slots: one per CTA of the per-column panel launches, plus two
+// per CTA of the cooperative panel (alternating by column parity).
+constexpr size_t panel_nparts(int64_t n) {
+  return (size_t)(((n > 1 ? n : 1) + PANEL_T - 1) / PANEL_T) + 1 + 2 * COOP_GMAX;
+}
+
+// Panel widths above this use the per-column panel launches.
+constexpr int COOP_NB_MAX = 256;
+
+// Workspace of getrf for order n and panel width nb (everything except the
+// Ozaki engine's slices): header, pivot partials, multiplier buffer, the
+// cooperative panel's row slots, and for 3M the pre-summed planes.
 template <int L>
 constexpr size_t getrf_ws_bytes(int64_t n, int nb, bool m3) {
-  size_t nparts = (size_t)(((n > 1 ? n : 1) + PANEL_T - 1) / PANEL_T) + 1;
-  size_t b = 4 * 256;                                           // counter, info, zflag, recip
-  b += ((nparts * L * sizeof(double)) + 255) & ~(size_t)255;   // part_key
-  b += ((nparts * sizeof(int)) + 255) & ~(size_t)255;          // part_idx
+  const size_t nparts = panel_nparts(n);
+  const size_t nbc = (size_t)(nb < COOP_NB_MAX ? nb : COOP_NB_MAX);
+  size_t b = 4 * 256;                                              // counter, info, zflag, recip, barrier
+  b += ((nparts * L * sizeof(double)) + 255) & ~(size_t)255;      // part_key
+  b += ((nparts * sizeof(int)) + 255) & ~(size_t)255;             // part_idx
   b += ((nparts * 2 * L * sizeof(double)) + 255) & ~(size_t)255;  // part_rcp
-  b += ((2 * 2 * L * (size_t)n * sizeof(double)) + 255) & ~(size_t)255;  // lbuf
-  if (m3) b += 2 * (((size_t)n * nb * L * sizeof(double)) + 255);         // 3M pre-sums
+  b += ((2 * 2 * L * (size_t)n * sizeof(double)) + 255) & ~(size_t)255;              // lbuf
+  b += ((2 * COOP_GMAX * 2 * L * nbc * sizeof(double)) + 255) & ~(size_t)255;        // prow
+  b += ((2 * 2 * L * nbc * sizeof(double)) + 255) & ~(size_t)255;                    // srow
+  if (m3) b += 2 * ((((size_t)n * nb * L * sizeof(double)) + 255) & ~(size_t)255);  // 3M pre-sums
   return b + 1024;
 }
 
@@ -122,12 +137,13 @@ int launch_tri_block(dim3 grid, dim3 block, cudaStream_t s, View A, int64_t k0, 
 // CUDA error code.
 template <int L>
 int launch_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int32_t *ipiv, PanelWS<L> ws, CoopWS cw,
-                      size_t nparts, cudaStream_t s) {
+                      cudaStream_t s) {
   static int sms = 0, per_sm = -1;
   const int nb = (int)(jend - j0);
   const int64_t m = n - j0;
   if (sms == 0) sms = oz::sm_count();
-  int G = (int)std::min<int64_t>({(int64_t)sms, cdiv(m, 8), (int64_t)nparts});
+  if (nb > COOP_NB_MAX) return 1;
+  int G = (int)std::min<int64_t>({(int64_t)sms, cdiv(m, 8), (int64_t)COOP_GMAX});
   if (G < 1) G = 1;
   const int rpc = (int)cdiv(m, G);
   const size_t smem = (size_t)rpc * nb * 2 * L * sizeof(double);
@@ -211,9 +227,8 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   const bool ozk = method == MCLU_METHOD_OZAKI;
   Workspace w;
   const size_t oz_need = ozk ? oz::ws_bytes<L>(n, n, nb) : 0;
-  const size_t ws_need = getrf_ws_bytes<L>(n, m3 ? nb : 0, m3) + oz_need +
-                         (ozk ? (size_t)2 * L * nb * nb * sizeof(double) + 256 : 0) +
-                         2 * (((size_t)2 * 2 * L * nb * sizeof(double) + 255) & ~(size_t)255);
+  const size_t ws_need = getrf_ws_bytes<L>(n, nb, m3) + oz_need +
+                         (ozk ? (((size_t)2 * L * nb * nb * sizeof(double) + 255) & ~(size_t)255) : 0);
   char *ws_base = nullptr;
   if (ext_ws) {
     if (ext_bytes < ws_need) return MCLU_ERR_SCRATCH_CAPACITY;
@@ -229,24 +244,25 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   ws.info = (int *)(hdr + 256);
   ws.zflag = (int *)(hdr + 512);
   ws.recip = (double *)(hdr + 768);
-  size_t nparts = (size_t)cdiv(n, PANEL_T) + 1;
+  const size_t nparts = panel_nparts(n);
+  const size_t nbc = (size_t)std::min(nb, COOP_NB_MAX);
   ws.part_key = cv.take<double>(nparts * L);
   ws.part_idx = cv.take<int>(nparts);
   ws.part_rcp = cv.take<double>(nparts * 2 * L);
   ws.lbuf = cv.take<double>(2 * 2 * L * (size_t)n);
   ws.lbuf_ld = n;
+  CoopWS cw;
+  cw.bar_count = (unsigned *)(hdr + 640);
+  cw.bar_gen = (unsigned *)(hdr + 644);
+  cw.status = (int *)(hdr + 648);
+  cw.prow = cv.take<double>((size_t)2 * COOP_GMAX * 2 * L * nbc);
+  cw.srow = cv.take<double>((size_t)2 * 2 * L * nbc);
   double *sumL = nullptr, *sumU = nullptr;
   if (m3) {
     sumL = cv.take<double>((size_t)n * nb * L);
     sumU = cv.take<double>((size_t)n * nb * L);
   }
   void *oz_ws = ozk ? (void *)cv.take<char>(oz_need) : nullptr;
-  CoopWS cw;
-  cw.bar_count = (unsigned *)(hdr + 640);
-  cw.bar_gen = (unsigned *)(hdr + 644);
-  cw.status = (int *)(hdr + 648);
-  cw.prow = cv.take<double>((size_t)2 * 2 * L * nb);
-  cw.srow = cv.take<double>((size_t)2 * 2 * L * nb);
   double *winv = ozk ? cv.take<double>((size_t)2 * L * nb * nb) : nullptr;
   int *oz_status = ws.zflag + 1;  // spare word of the header block
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
@@ -256,7 +272,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     const int64_t jb = std::min<int64_t>(nb, n - j0), jend = j0 + jb;
     {  // panel: rows [j0, n), columns [j0, jend)
       ProfScope ps(PK_PANEL, s);
-      int rc = launch_panel_coop<L>(A, n, j0, jend, ipiv, ws, cw, nparts, s);
+      int rc = launch_panel_coop<L>(A, n, j0, jend, ipiv, ws, cw, s);
       if (rc == 1) {  // cooperative grid does not fit: one launch per column
         k_pivot_first<L><<<(unsigned)cdiv(n - j0, SEARCH_T), SEARCH_T, 0, s>>>(A, n, j0, j0, jend, ipiv, ws);
         MCLU_LAUNCHED();
@@ -269,18 +285,22 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
         return rc;
       }
     }
-    if (j0 > 0) {  // apply the panel's swaps to the columns on its left
+    if (n - jb > 0) {  // apply the panel's swaps to the columns left and right of it
       ProfScope ps(PK_LASWP, s);
-      k_laswp<L><<<(unsigned)cdiv(j0 * 2 * L, 256), 256, 0, s>>>(A, 0, j0, j0, jend, ipiv);
+      const size_t lsm = laswp_smem((int)jb);
+      if (lsm > 48 * 1024) {
+        static bool attr = false;
+        if (!attr) {
+          MCLU_TRY(cudaFuncSetAttribute(k_laswp_gather<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)laswp_smem(COOP_NB_MAX)));
+          attr = true;
+        }
+      }
+      k_laswp_gather<L><<<(unsigned)cdiv(n - jb, LASWP_C), 256, lsm, s>>>(A, n, j0, jend, ipiv);
       MCLU_LAUNCHED();
     }
     if (jend < n) {
       const int64_t n2 = n - jend;
-      {  // ... and on its right
-        ProfScope ps(PK_LASWP, s);
-        k_laswp<L><<<(unsigned)cdiv(n2 * 2 * L, 256), 256, 0, s>>>(A, jend, n, j0, jend, ipiv);
-        MCLU_LAUNCHED();
-      }
       {  // U12 = L11^{-1} A12
         ProfScope ps(PK_TRSM, s);
         const int RT = (int)((jb + 31) / 32 * 32);
@@ -297,8 +317,10 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
           View W{winv, jb, jb * jb};
           k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(W, jb);
           MCLU_LAUNCHED();
-          int rc0 = launch_tri_block<L, true, true, false>(dim3((unsigned)cdiv(jb, CT)), dim3(RT, CT), s, A, j0,
-                                                           (int)jb, W, jb, nullptr, 0, 0);
+          // one CTA per column of W: the block solve is FP64-pipe bound per
+          // SM, so the jb columns go to jb SMs
+          int rc0 = launch_tri_block<L, true, true, false>(dim3((unsigned)jb), dim3(RT, 1), s, A, j0, (int)jb, W,
+                                                           jb, nullptr, 0, 0);
           if (rc0) return rc0;
           int rc = oz::gemm<L>(false, W, View{Ap + jend * lda + j0, lda, lda * n}, View{Ap + jend * lda + j0, lda, lda * n},
                                jb, n2, jb, oz_ws, oz_status, s, note_launch);

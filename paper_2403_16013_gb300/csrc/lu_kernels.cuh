@@ -161,7 +161,7 @@ __device__ void finalize_pivot(View A, int64_t n, int64_t jp, int64_t j0, int64_
 // Block argmax of (key, row) that also publishes the reciprocal of the
 // winner's value into the block's partial q.
 template <int L>
-__device__ void write_partial(R<L> key, int idx, const Z<L> &rcp, PanelWS<L> ws, int q, int tid, int nthr) {
+__device__ int write_partial(R<L> key, int idx, const Z<L> &rcp, PanelWS<L> ws, int q, int tid, int nthr) {
   const int my_idx = idx;
   block_argmax<L>(key, idx, tid, nthr);
   __shared__ int s_w;
@@ -172,13 +172,15 @@ __device__ void write_partial(R<L> key, int idx, const Z<L> &rcp, PanelWS<L> ws,
     s_w = idx;
   }
   __syncthreads();
-  if (my_idx == s_w && my_idx != INT_MAX) {
+  const int w = s_w;
+  if (my_idx == w && my_idx != INT_MAX) {
 #pragma unroll
     for (int l = 0; l < L; l++) {
       ws.part_rcp[(int64_t)q * 2 * L + l] = rcp.re.x[l];
       ws.part_rcp[(int64_t)q * 2 * L + L + l] = rcp.im.x[l];
     }
   }
+  return w;
 }
 
 // True in exactly one CTA per launch: the last one to arrive.
@@ -332,22 +334,96 @@ __global__ void __launch_bounds__(PANEL_T *PANEL_T)
   }
 }
 
-// Apply the row swaps ipiv[k0..k1) to columns [c0, c1) (all 2L planes).
+// Apply the row swaps ipiv[k0..k1) of one panel to the columns outside it
+// (columns [0, k0) and [k1, n), numbered c' = 0 .. n - (k1 - k0) - 1), all
+// 2L planes.  The swaps only touch rows [k0, k1) and their partners p >= k,
+// so their product is a permutation of at most 2 (k1 - k0) rows: warp 0
+// composes it in shared memory (slot s < nb is row k0 + s, later slots hold
+// partner rows below k1; org[s] = the row whose content ends in slot s's row),
+// then every CTA gathers the moved rows of its LASWP_C columns into shared
+// memory and writes them back permuted.  Rows in [k0, k1) are contiguous in a
+// column (coalesced); partner rows cost one sector each.
+constexpr int LASWP_C = 16;  // columns per CTA
+
+inline size_t laswp_smem(int nb) {
+  return (size_t)2 * nb * (2 * sizeof(int) + LASWP_C * sizeof(double)) + 16;
+}
+
 template <int L>
-__global__ void k_laswp(View A, int64_t c0, int64_t c1, int64_t k0, int64_t k1, const int32_t *ipiv) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t ncols = c1 - c0;
-  if (t >= ncols * 2 * L) return;
-  const int64_t c = c0 + t % ncols;
-  const int pl = (int)(t / ncols);
-  double *P = A.p + (int64_t)pl * A.ps + c * A.ld;
-  for (int64_t k = k0; k < k1; k++) {
-    int64_t p = ipiv[k] - 1;
-    if (p != k) {
-      double a = P[k], b = P[p];
-      P[k] = b;
-      P[p] = a;
+__global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t n, int64_t k0, int64_t k1,
+                                                      const int32_t *ipiv) {
+  const int nb = (int)(k1 - k0);
+  extern __shared__ double lsm[];
+  double *vals = lsm;                                      // [2 nb][LASWP_C]
+  int *dst = reinterpret_cast<int *>(vals + (size_t)2 * nb * LASWP_C);  // [2 nb]
+  int *org = dst + 2 * nb;                                 // [2 nb]
+  __shared__ int s_cnt;
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int t = tid; t < nb; t += 256) {
+    dst[t] = (int)(k0 + t);
+    org[t] = (int)(k0 + t);
+  }
+  if (tid == 0) s_cnt = 0;
+  __syncthreads();
+  if (tid < 32) {
+    int cnt = 0;  // partner rows below k1 seen so far (slots nb .. nb + cnt - 1)
+    for (int k = 0; k < nb; k++) {
+      const int kk = (int)k0 + k;
+      const int p = ipiv[kk] - 1;
+      if (p == kk) continue;
+      int sp;
+      if (p < k1) {
+        sp = p - (int)k0;
+      } else {
+        sp = -1;
+        for (int base = 0; base < cnt && sp < 0; base += 32) {
+          const bool hit = base + lane < cnt && dst[nb + base + lane] == p;
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (m) sp = nb + base + __ffs(m) - 1;
+        }
+        if (sp < 0) {
+          sp = nb + cnt;
+          if (lane == 0) {
+            dst[sp] = p;
+            org[sp] = p;
+          }
+          cnt++;
+        }
+        __syncwarp();
+      }
+      if (lane == 0) {
+        const int t = org[k];
+        org[k] = org[sp];
+        org[sp] = t;
+      }
+      __syncwarp();
     }
+    if (lane == 0) s_cnt = cnt;
+  }
+  __syncthreads();
+  const int T = nb + s_cnt;
+  const int64_t ncols = n - nb;
+  const int64_t cb = (int64_t)blockIdx.x * LASWP_C;
+  for (int pl = 0; pl < 2 * L; pl++) {
+    double *P = A.p + (int64_t)pl * A.ps;
+    for (int t = tid; t < T * LASWP_C; t += 256) {
+      const int sl = t % T, cl = t / T;
+      const int64_t cc = cb + cl;
+      if (cc < ncols && org[sl] != dst[sl]) {
+        const int64_t c = cc < k0 ? cc : cc + nb;
+        vals[(size_t)sl * LASWP_C + cl] = P[c * A.ld + org[sl]];
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < T * LASWP_C; t += 256) {
+      const int sl = t % T, cl = t / T;
+      const int64_t cc = cb + cl;
+      if (cc < ncols && org[sl] != dst[sl]) {
+        const int64_t c = cc < k0 ? cc : cc + nb;
+        P[c * A.ld + dst[sl]] = vals[(size_t)sl * LASWP_C + cl];
+      }
+    }
+    __syncthreads();
   }
 }
 

@@ -25,7 +25,7 @@
 namespace {
 
 constexpr int64_t kNoallocMaxN = 8192;  // largest order this entry point accepts
-constexpr size_t kNoallocBytes = mclu::getrf_ws_bytes<2>(kNoallocMaxN, 0, false);
+constexpr size_t kNoallocBytes = mclu::getrf_ws_bytes<2>(kNoallocMaxN, 64, false);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 

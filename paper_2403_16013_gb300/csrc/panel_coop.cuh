@@ -4,16 +4,20 @@
 // One cooperative launch factors the whole panel rows [j0, n) x columns
 // [j0, jend): each CTA keeps a contiguous block of panel rows in shared
 // memory for all nb columns, so a column step needs no kernel launch and no
-// global-memory traffic except the pivot exchange.  Per column j:
+// global-memory traffic except the pivot exchange.  Per column j, with one
+// grid barrier:
 //   1. every CTA computes cabs1 keys of its rows i >= j and, speculatively,
 //      the reciprocal of each candidate; its best (key, row, reciprocal) goes
-//      to a global partial;                                  -> grid barrier
+//      to a global partial, its best row (all nb columns) to a global row
+//      slot, and the owner of row j also publishes row j;      -> grid barrier
 //   2. every CTA reduces all partials (same winner p everywhere; ties to the
-//      lowest row), the owner of row p publishes it as the pivot row and the
-//      owner of row j publishes row j;                        -> grid barrier
+//      lowest row) and reads the winner's row from its slot;
 //   3. the owners swap rows j and p in shared memory, every CTA scales its
 //      rows below j by the winner's reciprocal and applies the rank-1 update
 //      to the remaining panel columns.
+// Partials and row slots alternate between two buffers by column parity: a
+// buffer is rewritten two columns later, after a barrier that every CTA
+// reaches only once it has finished reading it.
 // Grid barriers are counter + generation in global memory with a bounded
 // spin (clock64 budget); a timeout sets *status and every CTA returns.
 #pragma once
@@ -23,14 +27,15 @@
 namespace mclu {
 
 constexpr int COOP_T = 256;
+constexpr int COOP_GMAX = 256;                  // most CTAs of one cooperative panel launch
 constexpr long long COOP_WAIT = 2000000000LL;  // ~1 s at 2 GHz
 
 struct CoopWS {
   unsigned *bar_count;  // arrival counter
   unsigned *bar_gen;    // generation
   int *status;          // nonzero: a barrier timed out
-  double *prow;         // [2][2L][nb] pivot row of the current column
-  double *srow;         // [2][2L][nb] displaced row j
+  double *prow;         // [2][G][nb][2L] best row of each CTA, by column parity
+  double *srow;         // [2][nb][2L] row j, by column parity
 };
 
 // Sense-reversal grid barrier with a bounded wait.  Returns false on timeout.
@@ -65,15 +70,18 @@ __device__ __forceinline__ bool coop_barrier(const CoopWS &cw, unsigned nblocks)
 
 // Factor panel columns [j0, jend) of rows [j0, n).  CTA b owns rows
 // [j0 + b*rpc, j0 + min((b+1)*rpc, n - j0)).  Shared memory: rpc x nb x 2L.
+// Partial slots: par * G + b for column parity par (2G slots).
 template <int L>
 __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int rpc,
                                                       int32_t *ipiv, PanelWS<L> ws, CoopWS cw) {
   extern __shared__ double sp[];  // [row][col][2L]
   const int tid = threadIdx.x;
   const int nb = (int)(jend - j0);
-  const int64_t rbeg = j0 + (int64_t)blockIdx.x * rpc;
+  const int G = (int)gridDim.x, b = (int)blockIdx.x;
+  const int64_t rbeg = j0 + (int64_t)b * rpc;
   const int64_t rend = min(n, rbeg + rpc);
   const int nr = (int)max((int64_t)0, rend - rbeg);
+  const int RW = nb * 2 * L;  // doubles per panel row
   auto at = [&](int r, int c) -> double * { return sp + ((size_t)r * nb + c) * 2 * L; };
   // load the owned rows
   for (int t = tid; t < nr * nb; t += COOP_T) {
@@ -90,6 +98,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
   __shared__ int s_p, s_zero, s_part;
   for (int jc = 0; jc < nb; jc++) {
     const int64_t j = j0 + jc;
+    const int par = jc & 1;
     // 1. keys and speculative reciprocals of the rows i >= j of this CTA
     R<L> key = invalid_key<L>();
     int idx = INT_MAX;
@@ -111,13 +120,24 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         rcp = z_inv<L>(a);
       }
     }
-    write_partial<L>(key, idx, rcp, ws, blockIdx.x, tid, COOP_T);
-    if (!coop_barrier(cw, gridDim.x)) return;
+    const int cand = write_partial<L>(key, idx, rcp, ws, par * G + b, tid, COOP_T);
+    // publish this CTA's best row and, from its owner, row j
+    if (cand != INT_MAX) {
+      double *dst = cw.prow + ((size_t)par * G + b) * RW;
+      const double *src = at((int)(cand - rbeg), 0);
+      for (int t = tid; t < RW; t += COOP_T) dst[t] = src[t];
+    }
+    if (j >= rbeg && j < rend) {
+      double *dst = cw.srow + (size_t)par * RW;
+      const double *src = at((int)(j - rbeg), 0);
+      for (int t = tid; t < RW; t += COOP_T) dst[t] = src[t];
+    }
+    if (!coop_barrier(cw, G)) return;
     // 2. reduce the partials (every CTA, same result)
     {
       R<L> bk = invalid_key<L>();
       int bi = INT_MAX, bq = -1;
-      for (int q = tid; q < (int)gridDim.x; q += COOP_T) {
+      for (int q = par * G + tid; q < par * G + G; q += COOP_T) {
         R<L> k;
 #pragma unroll
         for (int l = 0; l < L; l++) k.x[l] = __ldcg(ws.part_key + (int64_t)q * L + l);
@@ -141,30 +161,25 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     }
     const int64_t p = s_p;
     const bool zero = s_zero != 0;
-    const int slot = jc & 1;
-    double *prow = cw.prow + (size_t)slot * 2 * L * nb;
-    double *srow = cw.srow + (size_t)slot * 2 * L * nb;
-    // publish the pivot row (row p) and the displaced row j
-    if (p >= rbeg && p < rend) {
-      for (int t = tid; t < nb * 2 * L; t += COOP_T) prow[t] = at((int)(p - rbeg), t / (2 * L))[t % (2 * L)];
-    }
-    if (p != j && j >= rbeg && j < rend) {
-      for (int t = tid; t < nb * 2 * L; t += COOP_T) srow[t] = at((int)(j - rbeg), t / (2 * L))[t % (2 * L)];
-    }
-    if (blockIdx.x == 0 && tid == 0) {
+    if (b == 0 && tid == 0) {
       ipiv[j] = (int32_t)(p + 1);
       if (zero && *ws.info == 0) *ws.info = (int)(j + 1);
     }
-    if (!coop_barrier(cw, gridDim.x)) return;
+    if (zero) {  // nothing to eliminate in this column; no swap
+      __syncthreads();
+      continue;
+    }
+    const double *prow = cw.prow + (size_t)s_part * RW;  // row p as it stood before the swap
     // 3. swap in shared memory, then scale and update
     if (p != j) {
+      const double *srow = cw.srow + (size_t)par * RW;
       if (p >= rbeg && p < rend)
-        for (int t = tid; t < nb * 2 * L; t += COOP_T) at((int)(p - rbeg), t / (2 * L))[t % (2 * L)] = __ldcg(srow + t);
+        for (int t = tid; t < RW; t += COOP_T) at((int)(p - rbeg), 0)[t] = __ldcg(srow + t);
       if (j >= rbeg && j < rend)
-        for (int t = tid; t < nb * 2 * L; t += COOP_T) at((int)(j - rbeg), t / (2 * L))[t % (2 * L)] = __ldcg(prow + t);
+        for (int t = tid; t < RW; t += COOP_T) at((int)(j - rbeg), 0)[t] = __ldcg(prow + t);
     }
     __syncthreads();
-    if (!zero) {
+    {
       Z<L> r;
 #pragma unroll
       for (int q = 0; q < L; q++) {
@@ -189,7 +204,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         }
       }
       __syncthreads();
-      // rank-1 update of columns jc+1 .. nb-1 (pivot row read from the global copy)
+      // rank-1 update of columns jc+1 .. nb-1 (pivot row read from its global slot)
       const int ncol = nb - jc - 1;
       for (int t = tid; t < nr * ncol; t += COOP_T) {
         const int rr = t % nr, cc = jc + 1 + t / nr;
