@@ -389,6 +389,45 @@ int tri_solve(View A, int64_t n, const double *W, View R, View Y, int64_t nrhs, 
   return 0;
 }
 
+// The same substitution as one persistent cooperative launch per right-hand
+// side (k_trsv_flow).  flags: nblk ints, all below flagbase + 1 on entry.
+// Returns 1 when the grid cannot be co-resident (the caller falls back to
+// tri_solve).
+template <int L, bool LOWER, bool CONJT>
+int tri_solve_flow(View A, int64_t n, const double *W, View R, View Y, int64_t nrhs, int *flags, int flagbase,
+                   int *status, cudaStream_t s) {
+  static int sms = 0;
+  if (sms == 0) sms = oz::sm_count();
+  const int64_t nblk = cdiv(n, SOLVE_BS);
+  const int G = (int)std::min<int64_t>(sms, nblk);
+  const int nown = (int)cdiv(nblk, G);
+  const size_t smem = trsv_flow_smem<L>(nown);
+  if (smem > 200 * 1024) return 1;
+  if (smem > 48 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      MCLU_TRY(cudaFuncSetAttribute(k_trsv_flow<L, LOWER, CONJT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
+      attr = true;
+    }
+  }
+  int occ = 0;
+  MCLU_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trsv_flow<L, LOWER, CONJT>, FLOW_T, smem));
+  if ((int64_t)occ * sms < G) return 1;
+  for (int64_t c = 0; c < nrhs; c++) {
+    View Rc{R.p + c * R.ld, R.ld, R.ps}, Yc{Y.p + c * Y.ld, Y.ld, Y.ps};
+    int64_t a_n = n;
+    const double *a_W = W;
+    int *a_flags = flags, *a_status = status;
+    int a_val = flagbase + 1 + (int)c;
+    void *args[] = {&A, &a_n, &a_W, &Rc, &Yc, &a_flags, &a_val, &a_status};
+    MCLU_TRY(cudaLaunchCooperativeKernel((const void *)k_trsv_flow<L, LOWER, CONJT>, dim3(G), dim3(FLOW_T), args, smem,
+                                         s));
+    note_launch();
+  }
+  return 0;
+}
+
 template <int L>
 int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, const int32_t *ipiv, double *Bp,
           int64_t ldb, cudaStream_t s) {
@@ -413,9 +452,14 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
   const size_t rdiag_bytes = al((size_t)2 * L * n * sizeof(double));
   const size_t inv_bytes = al((size_t)nblk * 2 * L * BS * BS * sizeof(double));
   const size_t vec_bytes = al((size_t)2 * L * n * nrhs * sizeof(double));
+  const size_t flag_bytes = al((size_t)(nblk + 1) * sizeof(int));
+  if (2 * nrhs + 1 > INT32_MAX) return -3;
   Workspace w;
-  MCLU_TRY(w.alloc(perm_bytes + rdiag_bytes + 2 * inv_bytes + 2 * vec_bytes, s));
+  MCLU_TRY(w.alloc(perm_bytes + rdiag_bytes + 2 * inv_bytes + 2 * vec_bytes + flag_bytes, s));
   char *cur = (char *)w.p;
+  int *flags = (int *)cur;  // nblk step flags, then the status word
+  cur += flag_bytes;
+  MCLU_TRY(cudaMemsetAsync(flags, 0, (size_t)(nblk + 1) * sizeof(int), s));
   int32_t *perm = (int32_t *)cur;
   cur += perm_bytes;
   double *rdiag = (double *)cur;
@@ -441,18 +485,22 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
   if (!conj) {
     k_permute<L><<<pg, 256, 0, s>>>(B, X, perm, n, nrhs, 0);  // X = P B
     MCLU_LAUNCHED();
-    int rc = tri_solve<L, true, false>(A, n, WL, X, Y, nrhs, s);  // L y = P b
+    int rc = tri_solve_flow<L, true, false>(A, n, WL, X, Y, nrhs, flags, 0, flags + nblk, s);  // L y = P b
+    if (rc == 1) rc = tri_solve<L, true, false>(A, n, WL, X, Y, nrhs, s);
     if (rc) return rc;
-    rc = tri_solve<L, false, false>(A, n, WU, Y, X, nrhs, s);  // U x = y
+    rc = tri_solve_flow<L, false, false>(A, n, WU, Y, X, nrhs, flags, (int)nrhs, flags + nblk, s);  // U x = y
+    if (rc == 1) rc = tri_solve<L, false, false>(A, n, WU, Y, X, nrhs, s);
     if (rc) return rc;
     MCLU_TRY(cudaMemcpy2DAsync(Bp, ldb * sizeof(double), X.p, n * sizeof(double), n * sizeof(double),
                                (size_t)2 * L * nrhs, cudaMemcpyDeviceToDevice, s));
   } else {
     MCLU_TRY(cudaMemcpy2DAsync(X.p, n * sizeof(double), Bp, ldb * sizeof(double), n * sizeof(double),
                                (size_t)2 * L * nrhs, cudaMemcpyDeviceToDevice, s));
-    int rc = tri_solve<L, true, true>(A, n, WU, X, Y, nrhs, s);  // U^H w = b
+    int rc = tri_solve_flow<L, true, true>(A, n, WU, X, Y, nrhs, flags, 0, flags + nblk, s);  // U^H w = b
+    if (rc == 1) rc = tri_solve<L, true, true>(A, n, WU, X, Y, nrhs, s);
     if (rc) return rc;
-    rc = tri_solve<L, false, true>(A, n, WL, Y, X, nrhs, s);  // L^H z = w
+    rc = tri_solve_flow<L, false, true>(A, n, WL, Y, X, nrhs, flags, (int)nrhs, flags + nblk, s);  // L^H z = w
+    if (rc == 1) rc = tri_solve<L, false, true>(A, n, WL, Y, X, nrhs, s);
     if (rc) return rc;
     k_permute<L><<<pg, 256, 0, s>>>(X, B, perm, n, nrhs, 1);  // B = P^T z
     MCLU_LAUNCHED();

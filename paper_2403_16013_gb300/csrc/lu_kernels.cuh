@@ -547,7 +547,7 @@ __global__ void k_diag_recip(View A, int64_t n, double *rdiag, int64_t ld) {
 // (k_blk_inv); each block step is then one launch (k_blk_solve) that applies
 // the block's inverse to the current residual of the block and subtracts the
 // block's contribution from the remaining rows.
-constexpr int SOLVE_BS = 16;
+constexpr int SOLVE_BS = 8;
 
 // acc_re + i acc_im -= a b (complex, on the leveled accumulators)
 template <int L>
@@ -775,6 +775,255 @@ __global__ void __launch_bounds__(256) k_blk_solve(View A, int64_t k0, int bs, c
     z.re = are.result();
     z.im = aim.result();
     stz<L>(R, r, c, z);
+  }
+}
+
+// ------------------------------------- persistent dataflow substitution
+//
+// The whole forward (LOWER) or backward substitution of one right-hand side
+// in one cooperative launch.  Step q (q = 0 .. nblk-1) makes x of diagonal
+// block b(q) = q (LOWER) or nblk-1-q.  CTA g owns the steps q = g (mod G):
+// the residual of its blocks lives in its shared memory for the whole solve.
+// Iteration q of every CTA:
+//   1. get x_q: the owner has it; the others wait for flags[q] (acquire,
+//      bounded spin) and read it from Y;
+//   2. the owner of step q+1 (warp 0) subtracts op(T)(b(q+1), b(q)) x_q from
+//      its block, forms x_{q+1} = op(W_{b(q+1)}) r_{b(q+1)}, stores it in Y and
+//      releases flags[q+1] -- before any other work, since every CTA waits
+//      for it;
+//   3. all other owned blocks of later steps subtract op(T)(block, b(q)) x_q.
+// The owner of q+1 reads the T tile and W block for step 2 before it waits.
+// A wait that runs out (the co-resident cooperative launch rules this out)
+// sets *status and writes NaN to every x the CTA still owed, so the failure
+// shows in the result.
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr int FLOW_T = 128;
+constexpr long long FLOW_WAIT = 2000000000LL;  // bound on one flag wait, ~1 s at 2 GHz
+
+// One warp: lane = 4 i + g handles row i (< SOLVE_BS) and the products j = g, g+4.
+template <int L, bool CONJT>
+struct TileRegs {
+  Z<L> t[2];
+  __device__ __forceinline__ void load(View A, int64_t r0, int64_t c0, int br, int bc, int lane) {
+    const int i = lane >> 2, g = lane & 3;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int j = g + 4 * h;
+      t[h] = z_zero<L>();
+      if (i < br && j < bc) t[h] = CONJT ? z_conj<L>(ldz<L>(A, c0 + j, r0 + i)) : ldz<L>(A, r0 + i, c0 + j);
+    }
+  }
+};
+
+// res[i] -= sum_j T(i, j) x_j over one warp (combine of the 4 lanes of a row).
+template <int L>
+__device__ __forceinline__ void warp_tile_apply(const Z<L> (&t)[2], const double (*xs)[2 * L], double (*res)[2 * L],
+                                                int br, int bc, int lane) {
+  const int i = lane >> 2, g = lane & 3;
+  Acc<L> re, im;
+  re.zero();
+  im.zero();
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int j = g + 4 * h;
+    if (i < br && j < bc) acc_csub<L>(re, im, t[h], lds_z<L>(xs[j]));
+  }
+#pragma unroll
+  for (int off = 2; off > 0; off >>= 1) {
+    Acc<L> ore, oim;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      ore.s[q] = __shfl_down_sync(0xffffffffu, re.s[q], off, 4);
+      oim.s[q] = __shfl_down_sync(0xffffffffu, im.s[q], off, 4);
+    }
+    re.add_acc(ore, false);
+    im.add_acc(oim, false);
+  }
+  if (g == 0 && i < br) {
+    const Z<L> r0 = lds_z<L>(res[i]);
+    re.add(r0.re);
+    im.add(r0.im);
+    Z<L> z;
+    z.re = re.result();
+    z.im = im.result();
+    sts_z<L>(res[i], z);
+  }
+}
+
+// op(W) of one diagonal block, in the same lane layout (only the triangle).
+template <int L, bool LOWER, bool CONJT>
+struct InvRegs {
+  Z<L> w[2];
+  __device__ __forceinline__ void load(const double *Wb, int bs, int lane) {
+    constexpr int BS = SOLVE_BS;
+    const int i = lane >> 2, g = lane & 3;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int j = g + 4 * h;
+      w[h] = z_zero<L>();
+      if (i < bs && j < bs && (LOWER ? j <= i : j >= i)) {
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          if (CONJT) {
+            w[h].re.x[q] = Wb[((size_t)q * BS + j) * BS + i];
+            w[h].im.x[q] = -Wb[((size_t)(L + q) * BS + j) * BS + i];
+          } else {
+            w[h].re.x[q] = Wb[((size_t)q * BS + i) * BS + j];
+            w[h].im.x[q] = Wb[((size_t)(L + q) * BS + i) * BS + j];
+          }
+        }
+      }
+    }
+  }
+};
+
+// x = op(W) r over one warp; returns this lane's row result in lanes g == 0.
+template <int L>
+__device__ __forceinline__ void warp_inv_apply(const Z<L> (&w)[2], const double (*r)[2 * L], double (*x)[2 * L],
+                                               int bs, int lane) {
+  const int i = lane >> 2, g = lane & 3;
+  Acc<L> re, im;
+  re.zero();
+  im.zero();
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int j = g + 4 * h;
+    if (i < bs && j < bs) acc_cadd<L>(re, im, w[h], lds_z<L>(r[j]));
+  }
+#pragma unroll
+  for (int off = 2; off > 0; off >>= 1) {
+    Acc<L> ore, oim;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      ore.s[q] = __shfl_down_sync(0xffffffffu, re.s[q], off, 4);
+      oim.s[q] = __shfl_down_sync(0xffffffffu, im.s[q], off, 4);
+    }
+    re.add_acc(ore, false);
+    im.add_acc(oim, false);
+  }
+  if (g == 0 && i < bs) {
+    Z<L> z;
+    z.re = re.result();
+    z.im = im.result();
+    sts_z<L>(x[i], z);
+  }
+}
+
+// Shared memory of k_trsv_flow for nown owned blocks.
+template <int L>
+constexpr size_t trsv_flow_smem(int nown) {
+  return ((size_t)nown + 2) * SOLVE_BS * 2 * L * sizeof(double);
+}
+
+template <int L, bool LOWER, bool CONJT>
+__global__ void __launch_bounds__(FLOW_T) k_trsv_flow(View A, int64_t n, const double *Winv, View R, View Y,
+                                                      int *flags, int flagval, int *status) {
+  constexpr int BS = SOLVE_BS;
+  extern __shared__ double fsm[];
+  const int G = (int)gridDim.x, g = (int)blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nblk = (int)((n + BS - 1) / BS);
+  const int nown = (nblk - g + G - 1) / G;  // owned steps q = g + i G, i < nown
+  double(*res)[BS][2 * L] = reinterpret_cast<double(*)[BS][2 * L]>(fsm);
+  double(*xs)[BS][2 * L] = res + nown;  // [2][BS][2L], by step parity
+  __shared__ int s_ok;
+  auto blk = [&](int q) -> int64_t { return LOWER ? q : nblk - 1 - q; };
+  auto rows = [&](int q) -> int { return (int)min((int64_t)BS, n - blk(q) * BS); };
+  auto wblk = [&](int q) -> const double * { return Winv + blk(q) * 2 * L * BS * BS; };
+  auto publish = [&](int q, const double (*x)[2 * L]) {  // warp 0: store x_q, release flags[q]
+    if (lane < rows(q)) stz<L>(Y, blk(q) * BS + lane, 0, lds_z<L>(x[lane]));
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(flags + q, flagval);
+  };
+  auto fail_rest = [&](int qfrom) {  // NaN into every x this CTA still owed
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int i = 0; i < nown; i++) {
+      const int q = g + i * G;
+      if (q < qfrom) continue;
+      for (int t = tid; t < rows(q) * 2 * L; t += FLOW_T)
+        Y.p[(int64_t)(t / rows(q)) * Y.ps + blk(q) * BS + t % rows(q)] = nan;
+    }
+  };
+  for (int t = tid; t < nown * BS; t += FLOW_T) {
+    const int i = t / BS, r = t % BS, q = g + i * G;
+    const int64_t row = blk(q) * BS + r;
+    sts_z<L>(res[i][r], r < rows(q) ? ldz<L>(R, row, 0) : z_zero<L>());
+  }
+  __syncthreads();
+  if (g == 0 && warp == 0) {  // step 0 needs no update
+    InvRegs<L, LOWER, CONJT> w;
+    w.load(wblk(0), rows(0), lane);
+    warp_inv_apply<L>(w.w, res[0], xs[0], rows(0), lane);
+    __syncwarp();
+    publish(0, xs[0]);
+  }
+  __syncthreads();
+  for (int q = 0; q < nblk; q++) {
+    const int par = q & 1;
+    const int qn = q + 1;
+    const bool crit = qn < nblk && qn % G == g;
+    TileRegs<L, CONJT> tcrit;
+    InvRegs<L, LOWER, CONJT> wcrit;
+    if (crit && warp == 0) {  // operands of step 2, read before the wait
+      tcrit.load(A, blk(qn) * BS, blk(q) * BS, rows(qn), rows(q), lane);
+      wcrit.load(wblk(qn), rows(qn), lane);
+    }
+    if (q % G != g) {  // 1. wait for x_q
+      if (tid == 0) {
+        int ok = 1;
+        const long long t0 = clock64();
+        while (ld_acquire(flags + q) != flagval) {
+          if (clock64() - t0 > FLOW_WAIT) {
+            ok = 0;
+            atomicOr(status, 1);
+            break;
+          }
+        }
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (!s_ok) {
+        fail_rest(q);
+        return;
+      }
+      const int rq = rows(q);
+      for (int t = tid; t < rq * 2 * L; t += FLOW_T)
+        xs[par][t % rq][t / rq] = __ldcg(Y.p + (int64_t)(t / rq) * Y.ps + blk(q) * BS + t % rq);
+      __syncthreads();
+    }
+    // 2. the next step's block first
+    if (crit && warp == 0) {
+      const int i = (qn - g) / G;
+      warp_tile_apply<L>(tcrit.t, xs[par], res[i], rows(qn), rows(q), lane);
+      __syncwarp();
+      warp_inv_apply<L>(wcrit.w, res[i], xs[par ^ 1], rows(qn), lane);
+      __syncwarp();
+      publish(qn, xs[par ^ 1]);
+    }
+    // 3. the other owned blocks of later steps
+    {
+      int k = 0;
+      for (int i = 0; i < nown; i++) {
+        const int q2 = g + i * G;
+        if (q2 <= q || (crit && q2 == qn)) continue;
+        const int wk = crit ? 1 + k % (FLOW_T / 32 - 1) : k % (FLOW_T / 32);
+        k++;
+        if (warp != wk) continue;
+        TileRegs<L, CONJT> t;
+        t.load(A, blk(q2) * BS, blk(q) * BS, rows(q2), rows(q), lane);
+        warp_tile_apply<L>(t.t, xs[par], res[i], rows(q2), rows(q), lane);
+      }
+    }
+    __syncthreads();
   }
 }
 
