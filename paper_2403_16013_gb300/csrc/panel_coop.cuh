@@ -69,12 +69,14 @@ __device__ __forceinline__ bool coop_barrier(const CoopWS &cw, unsigned nblocks)
 }
 
 // Factor panel columns [j0, jend) of rows [j0, n).  CTA b owns rows
-// [j0 + b*rpc, j0 + min((b+1)*rpc, n - j0)).  Shared memory: rpc x nb x 2L.
-// Partial slots: par * G + b for column parity par (2G slots).
+// [j0 + b*rpc, j0 + min((b+1)*rpc, n - j0)).  Shared memory: the owned rows,
+// [col][component][row] with the row fastest (consecutive threads take
+// consecutive rows: no bank conflicts), then the pivot row of the current
+// column [col][component].  Partial slots: par * G + b for column parity par.
 template <int L>
 __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int rpc,
                                                       int32_t *ipiv, PanelWS<L> ws, CoopWS cw) {
-  extern __shared__ double sp[];  // [row][col][2L]
+  extern __shared__ double sp[];
   const int tid = threadIdx.x;
   const int nb = (int)(jend - j0);
   const int G = (int)gridDim.x, b = (int)blockIdx.x;
@@ -82,17 +84,31 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
   const int64_t rend = min(n, rbeg + rpc);
   const int nr = (int)max((int64_t)0, rend - rbeg);
   const int RW = nb * 2 * L;  // doubles per panel row
-  auto at = [&](int r, int c) -> double * { return sp + ((size_t)r * nb + c) * 2 * L; };
+  double *su = sp + (size_t)rpc * RW;  // pivot row [col][2L]
+  auto ldp = [&](int r, int c) {
+    Z<L> z;
+    const double *d = sp + (size_t)c * 2 * L * rpc + r;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      z.re.x[q] = d[(size_t)q * rpc];
+      z.im.x[q] = d[(size_t)(L + q) * rpc];
+    }
+    return z;
+  };
+  auto stp = [&](int r, int c, const Z<L> &z) {
+    double *d = sp + (size_t)c * 2 * L * rpc + r;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      d[(size_t)q * rpc] = z.re.x[q];
+      d[(size_t)(L + q) * rpc] = z.im.x[q];
+    }
+  };
+  // element t = c * 2L + q of row r (the global row-slot format)
+  auto rowel = [&](int r, int t) -> double & { return sp[(size_t)t * rpc + r]; };
   // load the owned rows
   for (int t = tid; t < nr * nb; t += COOP_T) {
     const int r = t % nr, c = t / nr;
-    const Z<L> z = ldz<L>(A, rbeg + r, j0 + c);
-    double *d = at(r, c);
-#pragma unroll
-    for (int q = 0; q < L; q++) {
-      d[q] = z.re.x[q];
-      d[L + q] = z.im.x[q];
-    }
+    stp(r, c, ldz<L>(A, rbeg + r, j0 + c));
   }
   __syncthreads();
   __shared__ int s_p, s_zero, s_part;
@@ -106,13 +122,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     for (int r = tid; r < nr; r += COOP_T) {
       const int64_t i = rbeg + r;
       if (i < j) continue;
-      Z<L> a;
-      const double *d = at(r, jc);
-#pragma unroll
-      for (int q = 0; q < L; q++) {
-        a.re.x[q] = d[q];
-        a.im.x[q] = d[L + q];
-      }
+      const Z<L> a = ldp(r, jc);
       const R<L> k = pivot_key<L>(a);
       if (better<L>(k, (int)i, key, idx)) {
         key = k;
@@ -124,13 +134,13 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     // publish this CTA's best row and, from its owner, row j
     if (cand != INT_MAX) {
       double *dst = cw.prow + ((size_t)par * G + b) * RW;
-      const double *src = at((int)(cand - rbeg), 0);
-      for (int t = tid; t < RW; t += COOP_T) dst[t] = src[t];
+      const int r = (int)(cand - rbeg);
+      for (int t = tid; t < RW; t += COOP_T) dst[t] = rowel(r, t);
     }
     if (j >= rbeg && j < rend) {
       double *dst = cw.srow + (size_t)par * RW;
-      const double *src = at((int)(j - rbeg), 0);
-      for (int t = tid; t < RW; t += COOP_T) dst[t] = src[t];
+      const int r = (int)(j - rbeg);
+      for (int t = tid; t < RW; t += COOP_T) dst[t] = rowel(r, t);
     }
     if (!coop_barrier(cw, G)) return;
     // 2. reduce the partials (every CTA, same result)
@@ -169,14 +179,16 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       __syncthreads();
       continue;
     }
-    const double *prow = cw.prow + (size_t)s_part * RW;  // row p as it stood before the swap
-    // 3. swap in shared memory, then scale and update
+    // 3. stage the pivot row (row p before the swap), swap, scale, update
+    const double *prow = cw.prow + (size_t)s_part * RW;
+    for (int t = tid; t < RW; t += COOP_T) su[t] = __ldcg(prow + t);
+    __syncthreads();
     if (p != j) {
       const double *srow = cw.srow + (size_t)par * RW;
       if (p >= rbeg && p < rend)
-        for (int t = tid; t < RW; t += COOP_T) at((int)(p - rbeg), 0)[t] = __ldcg(srow + t);
+        for (int t = tid; t < RW; t += COOP_T) rowel((int)(p - rbeg), t) = __ldcg(srow + t);
       if (j >= rbeg && j < rend)
-        for (int t = tid; t < RW; t += COOP_T) at((int)(j - rbeg), 0)[t] = __ldcg(prow + t);
+        for (int t = tid; t < RW; t += COOP_T) rowel((int)(j - rbeg), t) = su[t];
     }
     __syncthreads();
     {
@@ -189,44 +201,21 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       // multipliers of the rows below j
       for (int rr = tid; rr < nr; rr += COOP_T) {
         if (rbeg + rr <= j) continue;
-        double *d = at(rr, jc);
-        Z<L> a;
-#pragma unroll
-        for (int q = 0; q < L; q++) {
-          a.re.x[q] = d[q];
-          a.im.x[q] = d[L + q];
-        }
-        const Z<L> l = z_mul<L>(a, r);
-#pragma unroll
-        for (int q = 0; q < L; q++) {
-          d[q] = l.re.x[q];
-          d[L + q] = l.im.x[q];
-        }
+        stp(rr, jc, z_mul<L>(ldp(rr, jc), r));
       }
       __syncthreads();
-      // rank-1 update of columns jc+1 .. nb-1 (pivot row read from its global slot)
+      // rank-1 update of columns jc+1 .. nb-1 with the staged pivot row
       const int ncol = nb - jc - 1;
       for (int t = tid; t < nr * ncol; t += COOP_T) {
         const int rr = t % nr, cc = jc + 1 + t / nr;
         if (rbeg + rr <= j) continue;
-        double *d = at(rr, cc);
-        const double *dl = at(rr, jc);
-        Z<L> a, l, u;
+        Z<L> u;
 #pragma unroll
         for (int q = 0; q < L; q++) {
-          a.re.x[q] = d[q];
-          a.im.x[q] = d[L + q];
-          l.re.x[q] = dl[q];
-          l.im.x[q] = dl[L + q];
-          u.re.x[q] = __ldcg(prow + (size_t)cc * 2 * L + q);
-          u.im.x[q] = __ldcg(prow + (size_t)cc * 2 * L + L + q);
+          u.re.x[q] = su[cc * 2 * L + q];
+          u.im.x[q] = su[cc * 2 * L + L + q];
         }
-        const Z<L> z = z_fms<L>(a, l, u);
-#pragma unroll
-        for (int q = 0; q < L; q++) {
-          d[q] = z.re.x[q];
-          d[L + q] = z.im.x[q];
-        }
+        stp(rr, cc, z_fms<L>(ldp(rr, cc), ldp(rr, jc), u));
       }
     }
     __syncthreads();
@@ -234,14 +223,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
   // write the owned rows back
   for (int t = tid; t < nr * nb; t += COOP_T) {
     const int r = t % nr, c = t / nr;
-    const double *d = at(r, c);
-    Z<L> z;
-#pragma unroll
-    for (int q = 0; q < L; q++) {
-      z.re.x[q] = d[q];
-      z.im.x[q] = d[L + q];
-    }
-    stz<L>(A, rbeg + r, j0 + c, z);
+    stz<L>(A, rbeg + r, j0 + c, ldp(r, c));
   }
 }
 
