@@ -135,6 +135,10 @@ template <int N>
 __device__ __forceinline__ uint32_t umma_idesc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
+// The same for a runtime N (a multiple of 16, 16 .. 256).
+__device__ __forceinline__ uint32_t umma_idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
@@ -697,7 +701,6 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // --------------------------------------------- MMA
-      const uint32_t idesc = umma_idesc<N>();
       uint32_t a_it = 0, r = 0;
       for (int64_t t = blockIdx.x; t < total && !s_err; t += gridDim.x) {
         for (int c = 0; c < nchunks; c++, r++) {
@@ -714,9 +717,16 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
             }
             tc_fence_after();
             const uint32_t a0 = smem_u32(sA + st * A_BYTES);
-            for (int q = 0; q < S - p; q++) {
-              const uint32_t b0 = smem_u32(sB + q * B_TILE);
-              const uint32_t d = tmem + (uint32_t)((p + q) * N);
+            // The S B slices lie back to back in one K-major, 128-byte-swizzled
+            // layout (each a multiple of 1024 bytes), so A_p times slices
+            // 0 .. S-1-p is one product with (S - p) N columns, landing on the
+            // TMEM column blocks of diagonals p .. S-1 (split at 256 columns).
+            const int ncols = (S - p) * N;
+            for (int c0 = 0; c0 < ncols; c0 += 256) {
+              const int nn = min(256, ncols - c0);
+              const uint32_t b0 = smem_u32(sB) + (uint32_t)(c0 * KC * 2);
+              const uint32_t d = tmem + (uint32_t)(p * N + c0);
+              const uint32_t idesc = umma_idesc_n(nn);
 #pragma unroll
               for (int ks = 0; ks < KC / 16; ks++)
                 umma_bf16(d, umma_desc(a0 + ks * 32), umma_desc(b0 + ks * 32), idesc, (p > 0 || ks > 0) ? 1u : 0u);
