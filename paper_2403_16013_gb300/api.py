@@ -93,15 +93,16 @@ def adjoint_rank1(lam: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
 
 
 _VEC_OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "cadd": 10, "csub": 11, "cmul": 12, "cmul3m": 13,
-            "cdiv": 14, "cinv": 15, "cabs1": 16}
+            "cdiv": 14, "cinv": 15, "cabs1": 16, "icmul": 20, "icfms": 21, "icabs1": 22, "icinv": 23}
 
 
-def vec_op(op: str, x: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
-    """Elementwise MC arithmetic: real ops on [L, count], complex ops on [2, L, count]."""
+def vec_op(op: str, x: torch.Tensor, y: torch.Tensor | None = None, z: torch.Tensor | None = None) -> torch.Tensor:
+    """Elementwise MC arithmetic: real ops on [L, count], complex ops on [2, L, count].
+    "icfms" computes z - x y (z is the third operand); the other ops ignore z."""
     code = _VEC_OPS[op]
     L = x.shape[0] if code < 10 else x.shape[1]
     count = x.shape[-1]
-    z = torch.empty_like(x)
+    z = z.clone() if (code == 21 and z is not None) else torch.empty_like(x)
     rc = B.vec_op(code, L, count, x.data_ptr(), 0 if y is None else y.data_ptr(), z.data_ptr(), _stream())
     B.check(rc, f"vec_op {op}")
     return z

@@ -598,12 +598,12 @@ int ozaki_split(int side, int64_t rows, int64_t cols, const double *X, int64_t l
 template <int L>
 int vec_op(int op, int64_t count, const double *x, const double *y, double *z, cudaStream_t s) {
   const bool real = op >= 0 && op <= 3;
-  const bool cplx = op >= 10 && op <= 16;
+  const bool cplx = (op >= 10 && op <= 16) || (op >= 20 && op <= 23);
   if (!real && !cplx) return -1;
   if (count < 0) return -3;
   if (count == 0) return 0;
   if (!x) return -4;
-  if (!y && op != 15 && op != 16) return -5;
+  if (!y && op != 15 && op != 16 && op != 22 && op != 23) return -5;
   if (!z) return -6;
   k_vec_op<L><<<(unsigned)cdiv(count, 128), 128, 0, s>>>(op, count, x, y, z);
   MCLU_LAUNCHED();
