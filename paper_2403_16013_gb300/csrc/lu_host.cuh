@@ -213,8 +213,8 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     if (opts->reserved != 0) return -6;
     if (method == MCLU_METHOD_OZAKI) {
       if (opts->ozaki_slices != 0 && opts->ozaki_slices != oz::Cfg<L>::S) return MCLU_ERR_UNSUPPORTED;
-      if (opts->nb == 0) nb = oz::NB_MAX;
-      if (nb > oz::NB_MAX) return -6;
+      if (opts->nb == 0) nb = 2 * oz::NB_MAX;
+      if (nb > 4 * oz::NB_MAX) return -6;
     }
   }
   if (n > INT32_MAX - 1) return -1;
@@ -268,36 +268,77 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
   View A{Ap, lda, lda * n};
 
-  for (int64_t j0 = 0; j0 < n; j0 += nb) {
-    const int64_t jb = std::min<int64_t>(nb, n - j0), jend = j0 + jb;
-    {  // panel: rows [j0, n), columns [j0, jend)
-      ProfScope ps(PK_PANEL, s);
-      int rc = launch_panel_coop<L>(A, n, j0, jend, ipiv, ws, cw, s);
-      if (rc == 1) {  // cooperative grid does not fit: one launch per column
-        k_pivot_first<L><<<(unsigned)cdiv(n - j0, SEARCH_T), SEARCH_T, 0, s>>>(A, n, j0, j0, jend, ipiv, ws);
+  // panel on rows [p0, n), columns [p0, p1): one cooperative launch, or one
+  // launch per column when the grid cannot be co-resident
+  auto panel = [&](int64_t p0, int64_t p1) -> int {
+    ProfScope ps(PK_PANEL, s);
+    int rc = launch_panel_coop<L>(A, n, p0, p1, ipiv, ws, cw, s);
+    if (rc == 1) {
+      k_pivot_first<L><<<(unsigned)cdiv(n - p0, SEARCH_T), SEARCH_T, 0, s>>>(A, n, p0, p0, p1, ipiv, ws);
+      MCLU_LAUNCHED();
+      for (int64_t j = p0; j < p1; j++) {
+        dim3 grid((unsigned)std::max<int64_t>(1, cdiv(n - j - 1, PANEL_T)), (unsigned)panel_colblocks(j, p1));
+        k_panel_step<L><<<grid, dim3(PANEL_T, PANEL_T), 0, s>>>(A, n, j, p0, p1, ipiv, ws);
         MCLU_LAUNCHED();
-        for (int64_t j = j0; j < jend; j++) {
-          dim3 grid((unsigned)std::max<int64_t>(1, cdiv(n - j - 1, PANEL_T)), (unsigned)panel_colblocks(j, jend));
-          k_panel_step<L><<<grid, dim3(PANEL_T, PANEL_T), 0, s>>>(A, n, j, j0, jend, ipiv, ws);
-          MCLU_LAUNCHED();
-        }
-      } else if (rc) {
-        return rc;
+      }
+      return 0;
+    }
+    return rc;
+  };
+  // the swaps ipiv[k0..k1) applied to columns [c0, c1) other than [x0, x1)
+  auto laswp = [&](int64_t k0, int64_t k1, int64_t c0, int64_t c1, int64_t x0, int64_t x1) -> int {
+    const int64_t ncols = (c1 - c0) - (x1 - x0);
+    if (ncols <= 0 || k1 <= k0) return 0;
+    ProfScope ps(PK_LASWP, s);
+    const size_t lsm = laswp_smem((int)(k1 - k0));
+    if (lsm > 48 * 1024) {
+      static bool attr = false;
+      if (!attr) {
+        MCLU_TRY(cudaFuncSetAttribute(k_laswp_gather<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)laswp_smem(COOP_NB_MAX)));
+        attr = true;
       }
     }
-    if (n - jb > 0) {  // apply the panel's swaps to the columns left and right of it
-      ProfScope ps(PK_LASWP, s);
-      const size_t lsm = laswp_smem((int)jb);
-      if (lsm > 48 * 1024) {
-        static bool attr = false;
-        if (!attr) {
-          MCLU_TRY(cudaFuncSetAttribute(k_laswp_gather<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)laswp_smem(COOP_NB_MAX)));
-          attr = true;
+    k_laswp_gather<L><<<(unsigned)cdiv(ncols, LASWP_C), 256, lsm, s>>>(A, k0, k1, ipiv, c0, c1, x0, x1);
+    MCLU_LAUNCHED();
+    return 0;
+  };
+
+  for (int64_t j0 = 0; j0 < n; j0 += nb) {
+    const int64_t jb = std::min<int64_t>(nb, n - j0), jend = j0 + jb;
+    if (!ozk) {
+      int rc = panel(j0, jend);
+      if (rc) return rc;
+    } else {
+      // Ozaki: the block is factored as sub-panels of oz::NB_MAX columns, each
+      // followed by the update of the block's remaining columns (their swaps,
+      // their U rows by the block solve, an Ozaki product for the rest), so
+      // that the trailing update below takes all jb columns in one product
+      // (K = 2 jb realified: several TMEM chunks, one exact C - P per element).
+      for (int64_t s0 = j0; s0 < jend; s0 += oz::NB_MAX) {
+        const int64_t send = std::min<int64_t>(s0 + oz::NB_MAX, jend), sb = send - s0;
+        int rc = panel(s0, send);
+        if (rc) return rc;
+        rc = laswp(s0, send, j0, s0, s0, s0);  // the block's earlier columns
+        if (rc) return rc;
+        if (send < jend) {
+          rc = laswp(s0, send, send, jend, jend, jend);  // the block's later columns
+          if (rc) return rc;
+          ProfScope ps(PK_OTHER, s);
+          View U{Ap + send * lda, lda, lda * n};  // rows s0.., columns send..jend
+          rc = launch_tri_block<L, true, true, false>(dim3((unsigned)(jend - send)), dim3((int)((sb + 31) / 32 * 32), 1),
+                                                      s, A, s0, (int)sb, U, jend - send, nullptr, 0, s0);
+          if (rc) return rc;
+          rc = oz::gemm<L>(true, View{Ap + s0 * lda + send, lda, lda * n}, View{Ap + send * lda + s0, lda, lda * n},
+                           View{Ap + send * lda + send, lda, lda * n}, n - send, jend - send, sb, oz_ws, oz_status, s,
+                           note_launch);
+          if (rc) return rc;
         }
       }
-      k_laswp_gather<L><<<(unsigned)cdiv(n - jb, LASWP_C), 256, lsm, s>>>(A, n, j0, jend, ipiv);
-      MCLU_LAUNCHED();
+    }
+    {  // apply the block's swaps to the columns left and right of it
+      int rc = laswp(j0, jend, 0, n, j0, jend);
+      if (rc) return rc;
     }
     if (jend < n) {
       const int64_t n2 = n - jend;

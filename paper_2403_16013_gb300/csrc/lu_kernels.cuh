@@ -335,15 +335,16 @@ __global__ void __launch_bounds__(PANEL_T *PANEL_T)
   }
 }
 
-// Apply the row swaps ipiv[k0..k1) of one panel to the columns outside it
-// (columns [0, k0) and [k1, n), numbered c' = 0 .. n - (k1 - k0) - 1), all
-// 2L planes.  The swaps only touch rows [k0, k1) and their partners p >= k,
-// so their product is a permutation of at most 2 (k1 - k0) rows: warp 0
-// composes it in shared memory (slot s < nb is row k0 + s, later slots hold
-// partner rows below k1; org[s] = the row whose content ends in slot s's row),
-// then every CTA gathers the moved rows of its LASWP_C columns into shared
-// memory and writes them back permuted.  Rows in [k0, k1) are contiguous in a
-// column (coalesced); partner rows cost one sector each.
+// Apply the row swaps ipiv[k0..k1) of one panel to the columns [c0, c1)
+// other than [x0, x1) (x0 = x1: none excluded; the excluded range lies inside
+// [c0, c1)), numbered c' = 0 .. ncols - 1, all 2L planes.  The swaps only
+// touch rows [k0, k1) and their partners p >= k, so their product is a
+// permutation of at most 2 (k1 - k0) rows: warp 0 composes it in shared
+// memory (slot s < nb is row k0 + s, later slots hold partner rows below k1;
+// org[s] = the row whose content ends in slot s's row), then every CTA
+// gathers the moved rows of its LASWP_C columns into shared memory and writes
+// them back permuted.  Rows in [k0, k1) are contiguous in a column
+// (coalesced); partner rows cost one sector each.
 constexpr int LASWP_C = 16;  // columns per CTA
 
 inline size_t laswp_smem(int nb) {
@@ -351,8 +352,8 @@ inline size_t laswp_smem(int nb) {
 }
 
 template <int L>
-__global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t n, int64_t k0, int64_t k1,
-                                                      const int32_t *ipiv) {
+__global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t k0, int64_t k1, const int32_t *ipiv,
+                                                      int64_t c0, int64_t c1, int64_t x0, int64_t x1) {
   const int nb = (int)(k1 - k0);
   extern __shared__ double lsm[];
   double *vals = lsm;                                      // [2 nb][LASWP_C]
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t n, int64_t
   }
   __syncthreads();
   const int T = nb + s_cnt;
-  const int64_t ncols = n - nb;
+  const int64_t ncols = (c1 - c0) - (x1 - x0);
   const int64_t cb = (int64_t)blockIdx.x * LASWP_C;
   for (int pl = 0; pl < 2 * L; pl++) {
     double *P = A.p + (int64_t)pl * A.ps;
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t n, int64_t
       const int sl = t % T, cl = t / T;
       const int64_t cc = cb + cl;
       if (cc < ncols && org[sl] != dst[sl]) {
-        const int64_t c = cc < k0 ? cc : cc + nb;
+        const int64_t c = (c0 + cc < x0) ? c0 + cc : c0 + cc + (x1 - x0);
         vals[(size_t)sl * LASWP_C + cl] = P[c * A.ld + org[sl]];
       }
     }
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t n, int64_t
       const int sl = t % T, cl = t / T;
       const int64_t cc = cb + cl;
       if (cc < ncols && org[sl] != dst[sl]) {
-        const int64_t c = cc < k0 ? cc : cc + nb;
+        const int64_t c = (c0 + cc < x0) ? c0 + cc : c0 + cc + (x1 - x0);
         P[c * A.ld + dst[sl]] = vals[(size_t)sl * LASWP_C + cl];
       }
     }

@@ -107,10 +107,13 @@ def test_zgemm_ozaki_against_exact(api, orc, L, beta_mode):
 
 
 @pytest.mark.parametrize("L", [2, 3, 4])
-def test_lu_ozaki_parity(api, orc, L):
+@pytest.mark.parametrize("nb", [0, 96])
+def test_lu_ozaki_parity(api, orc, L, nb):
+    """Default block (64: two 32-column sub-panels with an Ozaki update between
+    them) and 96 (three sub-panels), ragged last block."""
     n = 200 if L < 4 else 150
     A = inputs.gaussian_matrix(n, L, seed=1)
-    LU, ipiv, info = api.lu_factor(dev(A), method="ozaki")
+    LU, ipiv, info = api.lu_factor(dev(A), method="ozaki", nb=nb)
     assert int(host(info)[0]) == 0
     LUo, ipo, _, gap = orc.zgetrf(A)
     ipg = host(ipiv)
@@ -126,8 +129,9 @@ def test_lu_ozaki_parity(api, orc, L):
 
 
 @pytest.mark.parametrize("L", [2, 4])
-def test_lu_ozaki_known_factor_bit_exact(api, L):
+@pytest.mark.parametrize("nb", [16, 64])
+def test_lu_ozaki_known_factor_bit_exact(api, L, nb):
     A, ipiv_ref, packed, xr, xi = known_factor_case(40, L, seed=110)
-    LU, ipiv, info = api.lu_factor(dev(A), method="ozaki", nb=16)
+    LU, ipiv, info = api.lu_factor(dev(A), method="ozaki", nb=nb)
     assert np.array_equal(host(ipiv), ipiv_ref)
     assert np.array_equal(host(LU), packed)
