@@ -8,7 +8,7 @@ hot path.  value = steps * 8 n^3 / 3 / elapsed, summed over ranks (each rank
 an independent replica; the path has no data exchange).
 
 The default step uses the Ozaki-scheme trailing update on the tensor cores
-(nb = 64, factored as two 32-column sub-panels); the same step with the
+(nb = 128, factored as four 32-column sub-panels); the same step with the
 plain FP64-pipe 4M update (nb = 64) is
 timed right after it and reported under "plain", with both backward errors,
 so that the speed-up is stated at equal accuracy.
@@ -72,7 +72,7 @@ def parse():
     p.add_argument("--prec", default="dd", choices=["dd", "td", "qd"])
     p.add_argument("--method", default="ozaki", choices=["4m", "3m", "unblocked", "ozaki"])
     p.add_argument("--n", type=int, default=4096)
-    p.add_argument("--nb", type=int, default=0, help="block width (0: 64)")
+    p.add_argument("--nb", type=int, default=0, help="block width (0: 128 for ozaki, 64 otherwise)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="skip the plain 4M comparison of an ozaki run")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -304,7 +304,7 @@ def main():
     build.build()
     binding.load()
     n, L, prec = args.n, LIMBS[args.prec], args.prec
-    nb_of = lambda m: args.nb if args.nb else 64
+    nb_of = lambda m: args.nb if args.nb else (128 if m == "ozaki" else 64)
     A_h, b_h = make_inputs(n, L)
     A0 = torch.from_numpy(A_h).cuda()
     b0 = torch.from_numpy(b_h).cuda()

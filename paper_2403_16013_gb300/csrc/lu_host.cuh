@@ -213,7 +213,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     if (opts->reserved != 0) return -6;
     if (method == MCLU_METHOD_OZAKI) {
       if (opts->ozaki_slices != 0 && opts->ozaki_slices != oz::Cfg<L>::S) return MCLU_ERR_UNSUPPORTED;
-      if (opts->nb == 0) nb = 2 * oz::NB_MAX;
+      if (opts->nb == 0) nb = 4 * oz::NB_MAX;  // 128: measured best at n = 4096 (64: -3%, 96: -1.3% DD)
       if (nb > 4 * oz::NB_MAX) return -6;
     }
   }

@@ -44,7 +44,7 @@ def test_full_size(api, orc, prec, method):
     A = inputs.gaussian_matrix(n, L, seed=1)
     b = inputs.complex_gaussian_vector(n, L, seed=2)
     Ad = dev(A)
-    LU, ipiv, info = api.lu_factor(Ad, method=method, nb=64)
+    LU, ipiv, info = api.lu_factor(Ad, method=method, nb=128 if method == "ozaki" else 64)
     x = api.lu_solve(LU, ipiv, dev(b))
     torch.cuda.synchronize()
     assert int(host(info)[0]) == 0

@@ -107,10 +107,10 @@ def test_zgemm_ozaki_against_exact(api, orc, L, beta_mode):
 
 
 @pytest.mark.parametrize("L", [2, 3, 4])
-@pytest.mark.parametrize("nb", [0, 96])
+@pytest.mark.parametrize("nb", [0, 64, 96])
 def test_lu_ozaki_parity(api, orc, L, nb):
-    """Default block (64: two 32-column sub-panels with an Ozaki update between
-    them) and 96 (three sub-panels), ragged last block."""
+    """Default block (128: four 32-column sub-panels with Ozaki updates between
+    them), 64 and 96 (ragged last blocks)."""
     n = 200 if L < 4 else 150
     A = inputs.gaussian_matrix(n, L, seed=1)
     LU, ipiv, info = api.lu_factor(dev(A), method="ozaki", nb=nb)
