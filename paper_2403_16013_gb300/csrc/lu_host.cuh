@@ -106,6 +106,7 @@ constexpr size_t getrf_ws_bytes(int64_t n, int nb, bool m3) {
   b += ((2 * 2 * L * (size_t)n * sizeof(double)) + 255) & ~(size_t)255;              // lbuf
   b += ((2 * COOP_GMAX * 2 * L * nbc * sizeof(double)) + 255) & ~(size_t)255;        // prow
   b += ((2 * 2 * L * nbc * sizeof(double)) + 255) & ~(size_t)255;                    // srow
+  b += ((2 * COOP_GMAX * sizeof(int)) + 255) & ~(size_t)255;                          // rcp_flag
   if (m3) b += 2 * ((((size_t)n * nb * L * sizeof(double)) + 255) & ~(size_t)255);  // 3M pre-sums
   return b + 1024;
 }
@@ -257,6 +258,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   cw.status = (int *)(hdr + 648);
   cw.prow = cv.take<double>((size_t)2 * COOP_GMAX * 2 * L * nbc);
   cw.srow = cv.take<double>((size_t)2 * 2 * L * nbc);
+  cw.rcp_flag = cv.take<int>((size_t)2 * COOP_GMAX);
   double *sumL = nullptr, *sumU = nullptr;
   if (m3) {
     sumL = cv.take<double>((size_t)n * nb * L);
@@ -266,6 +268,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   double *winv = ozk ? cv.take<double>((size_t)2 * L * nb * nb) : nullptr;
   int *oz_status = ws.zflag + 1;  // spare word of the header block
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
+  MCLU_TRY(cudaMemsetAsync(cw.rcp_flag, 0, (size_t)2 * COOP_GMAX * sizeof(int), s));
   View A{Ap, lda, lda * n};
 
   // panel on rows [p0, n), columns [p0, p1): one cooperative launch, or one

@@ -48,45 +48,91 @@ __device__ __forceinline__ bool better(const R<L> &ka, int ia, const R<L> &kb, i
   return ia < ib;
 }
 
-// Block-wide argmax; nthr is a power of two; result in (key, idx) of thread 0.
 template <int L>
-__device__ void block_argmax(R<L> &key, int &idx, int tid, int nthr) {
-  __shared__ double s_key[SEARCH_T * L];
-  __shared__ int s_idx[SEARCH_T];
+__device__ __forceinline__ R<L> invalid_key_() {
+  R<L> k;
 #pragma unroll
-  for (int l = 0; l < L; l++) s_key[tid * L + l] = key.x[l];
-  s_idx[tid] = idx;
-  __syncthreads();
-  for (int s = nthr / 2; s > 0; s >>= 1) {
-    if (tid < s) {
-      R<L> a, b;
+  for (int l = 0; l < L; l++) k.x[l] = 0.0;
+  k.x[0] = -1.0;
+  return k;
+}
+
+// Warp argmax of (key, idx) under `better` (value, then the lower index).
+// The leading limb decides almost always: its order key is reduced with two
+// 32-bit __reduce_max_sync steps and a ballot; when several lanes share the
+// largest leading limb, they are compared in full, one lane at a time.
+// Every lane returns the warp's winner.
+template <int L>
+__device__ __forceinline__ void warp_argmax(R<L> &key, int &idx) {
+  const unsigned long long u = (unsigned long long)order_key(key.x[0]) ^ 0x8000000000000000ULL;
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  unsigned cand = __ballot_sync(0xffffffffu, hi == mhi && lo == mlo);
+  int win = __ffs(cand) - 1;
+  // equal leading limbs: full comparison among the candidates (unless the
+  // largest leading limb is negative, i.e. every lane holds the invalid key)
+  if (__popc(cand) > 1 && mhi >= 0x80000000u) {
+    R<L> bk;
+    int bi;
 #pragma unroll
-      for (int l = 0; l < L; l++) {
-        a.x[l] = s_key[tid * L + l];
-        b.x[l] = s_key[(tid + s) * L + l];
-      }
-      int ia = s_idx[tid], ib = s_idx[tid + s];
-      if (better<L>(b, ib, a, ia)) {
+    for (int l = 0; l < L; l++) bk.x[l] = __shfl_sync(0xffffffffu, key.x[l], win);
+    bi = __shfl_sync(0xffffffffu, idx, win);
+    cand &= cand - 1;
+    while (cand) {
+      const int c = __ffs(cand) - 1;
+      cand &= cand - 1;
+      R<L> ck;
 #pragma unroll
-        for (int l = 0; l < L; l++) s_key[tid * L + l] = b.x[l];
-        s_idx[tid] = ib;
+      for (int l = 0; l < L; l++) ck.x[l] = __shfl_sync(0xffffffffu, key.x[l], c);
+      const int ci = __shfl_sync(0xffffffffu, idx, c);
+      if (better<L>(ck, ci, bk, bi)) {
+        bk = ck;
+        bi = ci;
+        win = c;
       }
     }
-    __syncthreads();
   }
-  if (tid == 0) {
 #pragma unroll
-    for (int l = 0; l < L; l++) key.x[l] = s_key[l];
-    idx = s_idx[0];
+  for (int l = 0; l < L; l++) key.x[l] = __shfl_sync(0xffffffffu, key.x[l], win);
+  idx = __shfl_sync(0xffffffffu, idx, win);
+}
+
+// Block-wide argmax; nthr a multiple of 32 (at most 1024); result in (key,
+// idx) of thread 0.  Each warp reduces with warp_argmax, the warp results
+// meet in shared memory and warp 0 reduces them.
+template <int L>
+__device__ void block_argmax(R<L> &key, int &idx, int tid, int nthr) {
+  __shared__ double s_key[32 * L];
+  __shared__ int s_idx[32];
+  const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+  warp_argmax<L>(key, idx);
+  if (lane == 0) {
+#pragma unroll
+    for (int l = 0; l < L; l++) s_key[warp * L + l] = key.x[l];
+    s_idx[warp] = idx;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    R<L> k = invalid_key_<L>();
+    int i = INT_MAX;
+    if (lane < nw) {
+#pragma unroll
+      for (int l = 0; l < L; l++) k.x[l] = s_key[lane * L + l];
+      i = s_idx[lane];
+    }
+    warp_argmax<L>(k, i);
+    if (lane == 0) {
+      key = k;
+      idx = i;
+    }
   }
   __syncthreads();
 }
 
 template <int L>
 __device__ __forceinline__ R<L> invalid_key() {
-  R<L> k = r_zero<L>();
-  k.x[0] = -1.0;
-  return k;
+  return invalid_key_<L>();
 }
 
 // Last-CTA finalisation of the pivot of column jp: reduce nparts partials,
@@ -182,6 +228,22 @@ __device__ int write_partial(R<L> key, int idx, const Z<L> &rcp, PanelWS<L> ws, 
     }
   }
   return w;
+}
+
+// Block argmax of (key, row) published as the block's partial q (key and
+// row only); returns the winning row to every thread.
+template <int L>
+__device__ int write_partial_key(R<L> key, int idx, PanelWS<L> ws, int q, int tid, int nthr) {
+  block_argmax<L>(key, idx, tid, nthr);
+  __shared__ int s_w;
+  if (tid == 0) {
+#pragma unroll
+    for (int l = 0; l < L; l++) ws.part_key[(int64_t)q * L + l] = key.x[l];
+    ws.part_idx[q] = idx;
+    s_w = idx;
+  }
+  __syncthreads();
+  return s_w;
 }
 
 // True in exactly one CTA per launch: the last one to arrive.

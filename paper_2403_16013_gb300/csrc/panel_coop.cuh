@@ -6,12 +6,15 @@
 // memory for all nb columns, so a column step needs no kernel launch and no
 // global-memory traffic except the pivot exchange.  Per column j, with one
 // grid barrier:
-//   1. every CTA computes cabs1 keys of its rows i >= j and, speculatively,
-//      the reciprocal of each candidate; its best (key, row, reciprocal) goes
-//      to a global partial, its best row (all nb columns) to a global row
-//      slot, and the owner of row j also publishes row j;      -> grid barrier
+//   1. every CTA computes cabs1 keys of its rows i >= j; its best (key, row)
+//      goes to a global partial, its best row (all nb columns) to a global
+//      row slot, and the owner of row j also publishes row j; the CTA then
+//      arrives at the grid barrier and, while the others arrive, computes the
+//      reciprocal of its best value and publishes it with a release flag
+//      stamped with the column;                                -> grid barrier
 //   2. every CTA reduces all partials (same winner p everywhere; ties to the
-//      lowest row) and reads the winner's row from its slot;
+//      lowest row), waits for the winner's reciprocal flag (bounded) and
+//      reads the winner's row from its slot;
 //   3. the owners swap rows j and p in shared memory, every CTA scales its
 //      rows below j by the winner's reciprocal and applies the rank-1 update
 //      to the remaining panel columns.
@@ -36,7 +39,48 @@ struct CoopWS {
   int *status;          // nonzero: a barrier timed out
   double *prow;         // [2][G][nb][2L] best row of each CTA, by column parity
   double *srow;         // [2][nb][2L] row j, by column parity
+  int *rcp_flag;        // [2G] column stamp (j + 1) of the reciprocal in each partial slot
 };
+
+// Split grid barrier: arrive returns the generation to wait for; wait spins
+// (bounded) until it has passed.  Returns false on timeout.
+__device__ __forceinline__ unsigned coop_arrive(const CoopWS &cw, unsigned nblocks) {
+  __shared__ unsigned s_gen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = cw.bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(cw.bar_count, 1u) == nblocks - 1) {
+      *cw.bar_count = 0;
+      __threadfence();
+      atomicAdd(cw.bar_gen, 1u);
+    }
+    s_gen = g;
+  }
+  __syncthreads();
+  return s_gen;
+}
+
+__device__ __forceinline__ bool coop_wait(const CoopWS &cw, unsigned g) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned *gen = cw.bar_gen;
+    const long long t0 = clock64();
+    while (*gen == g) {
+      if (clock64() - t0 > COOP_WAIT) {
+        ok = 0;
+        atomicOr(cw.status, 1);
+        break;
+      }
+    }
+    __threadfence();
+    s_ok = ok && (*(volatile int *)cw.status == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
 
 // Sense-reversal grid barrier with a bounded wait.  Returns false on timeout.
 __device__ __forceinline__ bool coop_barrier(const CoopWS &cw, unsigned nblocks) {
@@ -115,22 +159,19 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
   for (int jc = 0; jc < nb; jc++) {
     const int64_t j = j0 + jc;
     const int par = jc & 1;
-    // 1. keys and speculative reciprocals of the rows i >= j of this CTA
+    // 1. keys of the rows i >= j of this CTA
     R<L> key = invalid_key<L>();
     int idx = INT_MAX;
-    Z<L> rcp = z_zero<L>();
     for (int r = tid; r < nr; r += COOP_T) {
       const int64_t i = rbeg + r;
       if (i < j) continue;
-      const Z<L> a = ldp(r, jc);
-      const R<L> k = pivot_key<L>(a);
+      const R<L> k = pivot_key<L>(ldp(r, jc));
       if (better<L>(k, (int)i, key, idx)) {
         key = k;
         idx = (int)i;
-        rcp = z_inv<L>(a);
       }
     }
-    const int cand = write_partial<L>(key, idx, rcp, ws, par * G + b, tid, COOP_T);
+    const int cand = write_partial_key<L>(key, idx, ws, par * G + b, tid, COOP_T);
     // publish this CTA's best row and, from its owner, row j
     if (cand != INT_MAX) {
       double *dst = cw.prow + ((size_t)par * G + b) * RW;
@@ -142,7 +183,21 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       const int r = (int)(j - rbeg);
       for (int t = tid; t < RW; t += COOP_T) dst[t] = rowel(r, t);
     }
-    if (!coop_barrier(cw, G)) return;
+    const unsigned gen = coop_arrive(cw, G);
+    // the reciprocal of this CTA's candidate, while the other CTAs arrive;
+    // published with a release flag stamped with the column
+    if (tid == 0 && cand != INT_MAX) {
+      const Z<L> rc = z_inv<L>(ldp((int)(cand - rbeg), jc));
+      const int q = par * G + b;
+#pragma unroll
+      for (int l = 0; l < L; l++) {
+        ws.part_rcp[(int64_t)q * 2 * L + l] = rc.re.x[l];
+        ws.part_rcp[(int64_t)q * 2 * L + L + l] = rc.im.x[l];
+      }
+      __threadfence();
+      st_release(cw.rcp_flag + q, (int)(j + 1));
+    }
+    if (!coop_wait(cw, gen)) return;
     // 2. reduce the partials (every CTA, same result)
     {
       R<L> bk = invalid_key<L>();
@@ -179,7 +234,25 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       __syncthreads();
       continue;
     }
-    // 3. stage the pivot row (row p before the swap), swap, scale, update
+    // 3. wait for the winner's reciprocal (bounded), stage the pivot row
+    //    (row p before the swap), swap, scale, update
+    {
+      __shared__ int s_rok;
+      if (tid == 0) {
+        int ok = 1;
+        const long long t0 = clock64();
+        while (ld_acquire(cw.rcp_flag + s_part) != (int)(j + 1)) {
+          if (clock64() - t0 > COOP_WAIT) {
+            ok = 0;
+            atomicOr(cw.status, 1);
+            break;
+          }
+        }
+        s_rok = ok;
+      }
+      __syncthreads();
+      if (!s_rok) return;
+    }
     const double *prow = cw.prow + (size_t)s_part * RW;
     for (int t = tid; t < RW; t += COOP_T) su[t] = __ldcg(prow + t);
     __syncthreads();
