@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(PANEL_T *PANEL_T)
 constexpr int LASWP_C = 16;  // columns per CTA
 
 inline size_t laswp_smem(int nb) {
-  return (size_t)2 * nb * (2 * sizeof(int) + LASWP_C * sizeof(double)) + 16;
+  return (size_t)2 * nb * (2 * sizeof(int) + LASWP_C * sizeof(double)) + (size_t)nb * sizeof(int) + 16;
 }
 
 template <int L>
@@ -421,11 +421,13 @@ __global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t k0, int64_
   double *vals = lsm;                                      // [2 nb][LASWP_C]
   int *dst = reinterpret_cast<int *>(vals + (size_t)2 * nb * LASWP_C);  // [2 nb]
   int *org = dst + 2 * nb;                                 // [2 nb]
+  int *piv = org + 2 * nb;                                 // [nb] the pivots, read once
   __shared__ int s_cnt;
   const int tid = threadIdx.x, lane = tid & 31;
   for (int t = tid; t < nb; t += 256) {
     dst[t] = (int)(k0 + t);
     org[t] = (int)(k0 + t);
+    piv[t] = ipiv[k0 + t] - 1;
   }
   if (tid == 0) s_cnt = 0;
   __syncthreads();
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t k0, int64_
     int cnt = 0;  // partner rows below k1 seen so far (slots nb .. nb + cnt - 1)
     for (int k = 0; k < nb; k++) {
       const int kk = (int)k0 + k;
-      const int p = ipiv[kk] - 1;
+      const int p = piv[k];
       if (p == kk) continue;
       int sp;
       if (p < k1) {
@@ -491,6 +493,44 @@ __global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t k0, int64_
   }
 }
 
+// acc_re + i acc_im -= a b (complex, on the leveled accumulators)
+template <int L>
+__device__ __forceinline__ void acc_csub(Acc<L> &re, Acc<L> &im, const Z<L> &a, const Z<L> &b) {
+  re.template add_prod<true>(a.re, b.re);
+  re.template add_prod<false>(a.im, b.im);
+  im.template add_prod<true>(a.re, b.im);
+  im.template add_prod<true>(a.im, b.re);
+}
+
+// acc_re + i acc_im += a b
+template <int L>
+__device__ __forceinline__ void acc_cadd(Acc<L> &re, Acc<L> &im, const Z<L> &a, const Z<L> &b) {
+  re.template add_prod<false>(a.re, b.re);
+  re.template add_prod<true>(a.im, b.im);
+  im.template add_prod<false>(a.re, b.im);
+  im.template add_prod<false>(a.im, b.re);
+}
+
+template <int L>
+__device__ __forceinline__ Z<L> lds_z(const double *p) {
+  Z<L> z;
+#pragma unroll
+  for (int q = 0; q < L; q++) {
+    z.re.x[q] = p[q];
+    z.im.x[q] = p[L + q];
+  }
+  return z;
+}
+
+template <int L>
+__device__ __forceinline__ void sts_z(double *p, const Z<L> &z) {
+#pragma unroll
+  for (int q = 0; q < L; q++) {
+    p[q] = z.re.x[q];
+    p[L + q] = z.im.x[q];
+  }
+}
+
 // Triangular block solve T x = b for the bs x bs diagonal block of A at
 // (k0, k0) on columns of X (rows xrow0..xrow0+bs-1); rdiag (planes
 // [2L][rld]) holds 1/T_kk when the diagonal is not unit.  T = A (LOWER: unit or not) or,
@@ -529,12 +569,21 @@ __global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, c
       sR[t] = rdiag[(int64_t)q * rld + k0 + kk];
     }
   }
+  // row tx accumulates its updates on leveled accumulators and is
+  // renormalised once, at the step that finalises it
   Z<L> x;
-  if (ok) x = ldz<L>(X, xrow0 + tx, c);
+  Acc<L> are, aim;
+  if (ok) {
+    x = ldz<L>(X, xrow0 + tx, c);
+    are.set(x.re);
+    aim.set(x.im);
+  }
   __syncthreads();
   for (int s = 0; s < bs; s++) {
     const int k = LOWER ? s : bs - 1 - s;
     if (ok && tx == k) {
+      x.re = are.result();
+      x.im = aim.result();
       if (!UNIT) {  // multiply by the precomputed reciprocal of T_kk
         Z<L> r;
 #pragma unroll
@@ -567,7 +616,7 @@ __global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, c
         xk.re.x[q] = s_x[ty * 2 * L + q];
         xk.im.x[q] = s_x[ty * 2 * L + L + q];
       }
-      x = z_fms<L>(x, t, xk);
+      acc_csub<L>(are, aim, t, xk);
     }
     __syncthreads();
   }
@@ -612,44 +661,6 @@ __global__ void k_diag_recip(View A, int64_t n, double *rdiag, int64_t ld) {
 // the block's inverse to the current residual of the block and subtracts the
 // block's contribution from the remaining rows.
 constexpr int SOLVE_BS = 8;
-
-// acc_re + i acc_im -= a b (complex, on the leveled accumulators)
-template <int L>
-__device__ __forceinline__ void acc_csub(Acc<L> &re, Acc<L> &im, const Z<L> &a, const Z<L> &b) {
-  re.template add_prod<true>(a.re, b.re);
-  re.template add_prod<false>(a.im, b.im);
-  im.template add_prod<true>(a.re, b.im);
-  im.template add_prod<true>(a.im, b.re);
-}
-
-// acc_re + i acc_im += a b
-template <int L>
-__device__ __forceinline__ void acc_cadd(Acc<L> &re, Acc<L> &im, const Z<L> &a, const Z<L> &b) {
-  re.template add_prod<false>(a.re, b.re);
-  re.template add_prod<true>(a.im, b.im);
-  im.template add_prod<false>(a.re, b.im);
-  im.template add_prod<false>(a.im, b.re);
-}
-
-template <int L>
-__device__ __forceinline__ Z<L> lds_z(const double *p) {
-  Z<L> z;
-#pragma unroll
-  for (int q = 0; q < L; q++) {
-    z.re.x[q] = p[q];
-    z.im.x[q] = p[L + q];
-  }
-  return z;
-}
-
-template <int L>
-__device__ __forceinline__ void sts_z(double *p, const Z<L> &z) {
-#pragma unroll
-  for (int q = 0; q < L; q++) {
-    p[q] = z.re.x[q];
-    p[L + q] = z.im.x[q];
-  }
-}
 
 // Inverses of the diagonal blocks of the factors held in A: blockIdx.y = 0
 // gives inv(L_kk) of the unit lower triangle, blockIdx.y = 1 inv(U_kk) of the
