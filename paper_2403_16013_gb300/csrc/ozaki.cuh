@@ -54,18 +54,21 @@ struct Cfg;
 // the fold accumulator F; TW: words of the split integer T; RW: words of the
 // final C - P frame; GS: diagonals pre-combined in int64 (GS diagonals of at
 // most 2^24, shifted by beta each, stay below 2^60); EW: epilogue warps
-// (16 for DD's 32-column tiles, 8 for the 16-column TD/QD tiles: measured).
+// (16 for DD's 32-column tiles, 8 for the 16-column TD/QD tiles: measured);
+// EF: fold each group of diagonals as soon as its products are done (1) or
+// all groups after the last one (0) -- measured faster for DD, slower for
+// TD/QD.
 template <>
 struct Cfg<2> {
-  static constexpr int BETA = 8, S = 14, N = 32, FW = 5, TW = 4, RW = 6, GS = 5, EW = 16;
+  static constexpr int BETA = 8, S = 14, N = 32, FW = 5, TW = 4, RW = 6, GS = 5, EW = 16, EF = 1;
 };
 template <>
 struct Cfg<3> {
-  static constexpr int BETA = 7, S = 24, N = 16, FW = 7, TW = 6, RW = 8, GS = 6, EW = 8;
+  static constexpr int BETA = 7, S = 24, N = 16, FW = 7, TW = 6, RW = 8, GS = 6, EW = 8, EF = 0;
 };
 template <>
 struct Cfg<4> {
-  static constexpr int BETA = 7, S = 32, N = 16, FW = 9, TW = 8, RW = 10, GS = 6, EW = 8;
+  static constexpr int BETA = 7, S = 32, N = 16, FW = 9, TW = 8, RW = 10, GS = 6, EW = 8, EF = 0;
 };
 
 constexpr int KC = 64;         // realified K per chunk (32 complex columns of A)
@@ -594,12 +597,25 @@ __device__ __forceinline__ void finish2(const uint32_t (&F)[FW], int eF, const d
 
 // Fold diagonals D0 .. D0+G-1 (G = min(GS, S - D0)) of the TMEM accumulators
 // into F: G_c = sum_t D_{D0+t} 2^(beta (G-1-t)) exactly in int64, then one
-// multiword addition at shift beta (S - D0 - G).
+// multiword addition at shift beta (S - D0 - G).  Group g of diagonals is
+// complete once the products of A slices 0 .. D0+G-1 are done: the warp
+// waits for that group's commit barrier (lane 0 waits, the outcome is
+// broadcast so the warp stays converged for the .sync.aligned loads).
 template <int L, int NH, int D0>
-__device__ __forceinline__ void fold_diagonals(uint32_t (&F)[NH][Cfg<L>::FW], uint32_t tbase) {
+__device__ __forceinline__ bool fold_diagonals(uint32_t (&F)[NH][Cfg<L>::FW], uint32_t tbase, uint64_t *bar_grp,
+                                               uint32_t parity, int lane) {
   constexpr int S = Cfg<L>::S, N = Cfg<L>::N, BETA = Cfg<L>::BETA, FW = Cfg<L>::FW;
   constexpr int GS = Cfg<L>::GS;
   constexpr int G = (S - D0) < GS ? (S - D0) : GS;
+  if (Cfg<L>::EF || D0 == 0) {
+    constexpr int NGRP = (S + GS - 1) / GS;
+    int got = 0;
+    if (lane == 0) got = mbar_wait(&bar_grp[Cfg<L>::EF ? D0 / GS : NGRP - 1], parity) ? 1 : 0;
+    got = __shfl_sync(0xffffffffu, got, 0);
+    if (!got) return false;
+    __syncwarp();
+    tc_fence_after();
+  }
   long long g[NH];
 #pragma unroll
   for (int cc = 0; cc < NH; cc++) g[cc] = 0;
@@ -613,7 +629,10 @@ __device__ __forceinline__ void fold_diagonals(uint32_t (&F)[NH][Cfg<L>::FW], ui
   }
 #pragma unroll
   for (int cc = 0; cc < NH; cc++) fold64<FW, BETA *(S - D0 - G)>(F[cc], g[cc]);
-  if constexpr (D0 + G < S) fold_diagonals<L, NH, D0 + G>(F, tbase);
+  if constexpr (D0 + G < S)
+    return fold_diagonals<L, NH, D0 + G>(F, tbase, bar_grp, parity, lane);
+  else
+    return true;
 }
 
 // ---------------------------------------------------------------- GEMM --
@@ -639,7 +658,9 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
   uint8_t *sB = base;
   uint8_t *sA = base + B_BYTES;
   __shared__ __align__(8) uint64_t bar_afull[NST], bar_aempty[NST];
-  __shared__ __align__(8) uint64_t bar_bfull, bar_bempty, bar_accfull, bar_accempty;
+  __shared__ __align__(8) uint64_t bar_bfull, bar_bempty, bar_accempty;
+  constexpr int NGRP = (S + CF::GS - 1) / CF::GS;  // fold groups of diagonals
+  __shared__ __align__(8) uint64_t bar_grp[NGRP];
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_err;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -650,7 +671,7 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
     }
     mbar_init(&bar_bfull, 1);
     mbar_init(&bar_bempty, 1);
-    mbar_init(&bar_accfull, 1);
+    for (int i = 0; i < NGRP; i++) mbar_init(&bar_grp[i], 1);
     mbar_init(&bar_accempty, EPI_WARPS);
     s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -732,10 +753,12 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
                 umma_bf16(d, umma_desc(a0 + ks * 32), umma_desc(b0 + ks * 32), idesc, (p > 0 || ks > 0) ? 1u : 0u);
             }
             umma_commit(&bar_aempty[st]);
+            // diagonals of the group ending at p are complete: let the
+            // epilogue fold them while the later slices multiply
+            if ((p + 1) % CF::GS == 0 || p == S - 1) umma_commit(&bar_grp[p / CF::GS]);
           }
           if (s_err) break;
           umma_commit(&bar_bempty);
-          umma_commit(&bar_accfull);
         }
       }
     }
@@ -755,20 +778,13 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
         for (int w = 0; w < FW; w++) F[cc][w] = 0;
       bool ok = true;
       for (int c = 0; c < nchunks; c++, r++) {
-        // lane 0 waits; the outcome is broadcast so the warp stays converged
-        // for the .sync.aligned TMEM loads
-        int got = 0;
-        if (lane == 0) got = mbar_wait(&bar_accfull, r & 1) ? 1 : 0;
-        got = __shfl_sync(0xffffffffu, got, 0);
-        if (!got) {
+        // diagonal d sits in TMEM columns [d N, d N + N); each group is
+        // folded as soon as its commit barrier completes
+        if (!fold_diagonals<L, NH, 0>(F, tbase, bar_grp, r & 1, lane)) {
           if (lane == 0) s_err = 5;
           ok = false;
           break;
         }
-        __syncwarp();
-        tc_fence_after();
-        // diagonal d sits in TMEM columns [d N, d N + N)
-        fold_diagonals<L, NH, 0>(F, tbase);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar_accempty);
