@@ -77,6 +77,9 @@ def parse():
     p.add_argument("--no-plain", action="store_true", help="skip the plain 4M comparison of an ozaki run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle sample")
+    p.add_argument("--sweep", action="store_true",
+                   help="block-width sweep instead of the benchmark line: LU + solve GFLOP/s for every method "
+                        "and nb at --n (default 1024), plus the unblocked form; one JSON line per point")
     return p.parse_args()
 
 
@@ -291,10 +294,55 @@ def backward_error(api, A0, X, B0):
     return r / (anorm * xnorm)
 
 
+def run_sweep(args):
+    """Time-vs-K study of the blocked factorisation (the paper's Figs. 10/13/16
+    analogue): LU + solve GFLOP/s against the block width for each trailing
+    update, and the unblocked form, on one GPU."""
+    import torch
+    from paper_2403_16013_gb300 import api, binding, build
+    build.build()
+    binding.load()
+    n = args.n if args.n != 4096 else 1024
+    L, prec = LIMBS[args.prec], args.prec
+    A_h, b_h = make_inputs(n, L)
+    A0, b0 = torch.from_numpy(A_h).cuda(), torch.from_numpy(b_h).cuda()
+    A, x = torch.empty_like(A0), torch.empty_like(b0)
+    ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    points = [("unblocked", 0)]
+    for method in ("4m", "3m", "ozaki"):
+        for nb in (16, 32, 64, 96, 128, 192, 256):
+            if method == "ozaki" and nb > 128:
+                continue
+            points.append((method, nb))
+    for method, nb in points:
+        def step():
+            A.copy_(A0)
+            api.lu_factor_(A, ipiv, info, method=method, nb=nb)
+            x.copy_(b0)
+            api.lu_solve(A, ipiv, x, inplace=True)
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, args.steps)
+        e0.record()
+        for _ in range(reps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        print(json.dumps({"sweep": True, "n": n, "prec": prec, "method": method, "nb": nb if nb else n,
+                          "ms_per_step": ms, "value": 8.0 * n ** 3 / 3.0 / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+                          "info": int(info.item())}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     import torch
 
