@@ -50,6 +50,12 @@ LIMBS = {"dd": 2, "td": 3, "qd": 4}
 FP64_OPS_PEAK = 0.625e12
 # Ozaki-scheme engine: slices S per precision; kept pairs p + q <= S - 1.
 OZAKI_S = {"dd": 14, "td": 24, "qd": 32}
+# DRAM traffic of the trailing-update kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of the first trailing update of
+# the n = 4096 DD step: n2 = 3968 rows and columns, K = 256 realified).  It is
+# reported, scaled to the average trailing launch by n2^2, only while the
+# kernel source is the one it was taken on (sha1 of csrc/ozaki.cuh).
+OZ_TRAFFIC = {"dd": {"bytes": 971030272 + 477952256, "n2": 3968, "src_sha1": "cb83ea875dc66ff7beee53aa17073ebe7a24110c"}}
 # unit roundoff exponents: u = 2^-104 / 2^-157 / 2^-209
 U_EXP = {"dd": 104, "td": 157, "qd": 209}
 
@@ -247,8 +253,19 @@ def roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el
         per_launch = flops / (gemm_calls / steps)
         achieved = per_launch / (gemm_ms / gemm_calls * 1e-3) / 1e12
         peak, src = measured_bf16_peak()
+        traffic = None
+        cap = OZ_TRAFFIC.get(prec)
+        if cap and nb == 128 and n == 4096:
+            import hashlib
+            with open(os.path.join(ROOT, "paper_2403_16013_gb300", "csrc", "ozaki.cuh"), "rb") as f:
+                if hashlib.sha1(f.read()).hexdigest() == cap["src_sha1"]:
+                    n2s = [n - j0 - min(nb, n - j0) for j0 in range(0, n, nb)]
+                    n2s = [v for v in n2s if v > 0]
+                    traffic = cap["bytes"] * (sum(v * v for v in n2s) / len(n2s)) / cap["n2"] ** 2
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": src + " bf16 burst", "traffic": None,
+                "peak_source": src + " bf16 burst", "traffic": traffic,
+                "traffic_note": None if traffic is None else
+                "ncu dram read+write of the first trailing launch (n2 = 3968), scaled to the average launch by n2^2",
                 "kernel": f"k_oz_gemm<{L},beta> (+ split kernels, counted in its time)",
                 "flops_per_launch": per_launch, "avg_launch_ms": gemm_ms / gemm_calls,
                 "share_of_step": gemm_ms / el_ms}
