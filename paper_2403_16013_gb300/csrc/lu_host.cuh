@@ -147,7 +147,8 @@ int launch_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int32_t *ipiv
   int G = (int)std::min<int64_t>({(int64_t)sms, cdiv(m, 8), (int64_t)COOP_GMAX});
   if (G < 1) G = 1;
   const int rpc = (int)cdiv(m, G);
-  const size_t smem = ((size_t)rpc + 1) * nb * 2 * L * sizeof(double);  // owned rows + pivot row
+  // owned rows + pivot row + the multipliers' partial products
+  const size_t smem = (((size_t)rpc + 1) * nb * 2 * L + (size_t)4 * rpc * L) * sizeof(double);
   if (smem > 200 * 1024) return 1;
   if (per_sm < 0) {
     MCLU_TRY(cudaFuncSetAttribute(k_panel_coop<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));

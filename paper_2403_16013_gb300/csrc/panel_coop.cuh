@@ -116,7 +116,8 @@ __device__ __forceinline__ bool coop_barrier(const CoopWS &cw, unsigned nblocks)
 // [j0 + b*rpc, j0 + min((b+1)*rpc, n - j0)).  Shared memory: the owned rows,
 // [col][component][row] with the row fastest (consecutive threads take
 // consecutive rows: no bank conflicts), then the pivot row of the current
-// column [col][component].  Partial slots: par * G + b for column parity par.
+// column [col][component], then the multipliers' four partial products
+// [4][row][L].  Partial slots: par * G + b for column parity par.
 template <int L>
 __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int rpc,
                                                       int32_t *ipiv, PanelWS<L> ws, CoopWS cw) {
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
   const int nr = (int)max((int64_t)0, rend - rbeg);
   const int RW = nb * 2 * L;  // doubles per panel row
   double *su = sp + (size_t)rpc * RW;  // pivot row [col][2L]
+  double *mscr = su + RW;              // [4][rpc][L] the multipliers' partial products
   auto ldp = [&](int r, int c) {
     Z<L> z;
     const double *d = sp + (size_t)c * 2 * L * rpc + r;
@@ -271,10 +273,40 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         r.re.x[q] = __ldcg(ws.part_rcp + (int64_t)s_part * 2 * L + q);
         r.im.x[q] = __ldcg(ws.part_rcp + (int64_t)s_part * 2 * L + L + q);
       }
-      // multipliers of the rows below j
-      for (int rr = tid; rr < nr; rr += COOP_T) {
-        if (rbeg + rr <= j) continue;
-        stp(rr, jc, z_mul<L>(ldp(rr, jc), r));
+      // multipliers l = a r of the rows below j: warps 0..3 (one per SMSP,
+      // each with its own FP64 unit) form the four real products
+      // Re a Re r, Im a Im r, Re a Im r, Im a Re r on leveled accumulators;
+      // warps 0 and 1 then form Re l = P0 - P1 and Im l = P2 + P3
+      {
+        const int w = tid >> 5, lane = tid & 31;
+        if (w < 4) {
+          const R<L> y = (w == 0 || w == 3) ? r.re : r.im;
+          for (int rr = lane; rr < nr; rr += 32) {
+            if (rbeg + rr <= j) continue;
+            const Z<L> a = ldp(rr, jc);
+            Acc<L> t;
+            t.set_prod((w == 0 || w == 2) ? a.re : a.im, y);
+#pragma unroll
+            for (int q = 0; q < L; q++) mscr[((size_t)w * rpc + rr) * L + q] = t.s[q];
+          }
+        }
+        __syncthreads();
+        if (w < 2) {
+          for (int rr = lane; rr < nr; rr += 32) {
+            if (rbeg + rr <= j) continue;
+            Acc<L> t, o;
+#pragma unroll
+            for (int q = 0; q < L; q++) {
+              t.s[q] = mscr[((size_t)(2 * w) * rpc + rr) * L + q];
+              o.s[q] = mscr[((size_t)(2 * w + 1) * rpc + rr) * L + q];
+            }
+            t.add_acc(o, w == 0);
+            const R<L> v = t.result();
+            double *d = sp + (size_t)jc * 2 * L * rpc + rr + (size_t)(w * L) * rpc;
+#pragma unroll
+            for (int q = 0; q < L; q++) d[(size_t)q * rpc] = v.x[q];
+          }
+        }
       }
       __syncthreads();
       // rank-1 update of columns jc+1 .. nb-1 with the staged pivot row
