@@ -186,18 +186,51 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       for (int t = tid; t < RW; t += COOP_T) dst[t] = rowel(r, t);
     }
     const unsigned gen = coop_arrive(cw, G);
-    // the reciprocal of this CTA's candidate, while the other CTAs arrive;
-    // published with a release flag stamped with the column
-    if (tid == 0 && cand != INT_MAX) {
-      const Z<L> rc = z_inv<L>(ldp((int)(cand - rbeg), jc));
+    // the reciprocal 1/p = conj(p) / |p|^2 of this CTA's candidate, while the
+    // other CTAs arrive, split over warps 0 and 1 (two SMSPs, two FP64
+    // units): Re p^2 and Im p^2 in parallel, the real reciprocal x of |p|^2
+    // on warp 0, then Re p x and -Im p x in parallel; published with a
+    // release flag stamped with the column
+    {
+      __shared__ double s_inv[2 * L];  // Im p^2 accumulator, then x
+      const int w = tid >> 5, lane = tid & 31;
+      const bool has = cand != INT_MAX;  // uniform over the CTA
+      const bool act = has && lane == 0 && w < 2;
       const int q = par * G + b;
+      Z<L> pv;
+      Acc<L> t;
+      if (act) {
+        pv = ldp((int)(cand - rbeg), jc);
+        const R<L> h = w == 0 ? pv.re : pv.im;
+        t.set_prod(h, h);
+        if (w == 1) {
 #pragma unroll
-      for (int l = 0; l < L; l++) {
-        ws.part_rcp[(int64_t)q * 2 * L + l] = rc.re.x[l];
-        ws.part_rcp[(int64_t)q * 2 * L + L + l] = rc.im.x[l];
+          for (int l = 0; l < L; l++) s_inv[l] = t.s[l];
+        }
       }
-      __threadfence();
-      st_release(cw.rcp_flag + q, (int)(j + 1));
+      __syncthreads();
+      if (has && tid == 0) {
+        Acc<L> o;
+#pragma unroll
+        for (int l = 0; l < L; l++) o.s[l] = s_inv[l];
+        t.add_acc(o, false);
+        const R<L> x = r_recip<L>(t.result());
+#pragma unroll
+        for (int l = 0; l < L; l++) s_inv[L + l] = x.x[l];
+      }
+      __syncthreads();
+      if (act) {
+        R<L> x;
+#pragma unroll
+        for (int l = 0; l < L; l++) x.x[l] = s_inv[L + l];
+        R<L> v = r_mul<L>(w == 0 ? pv.re : pv.im, x);
+        if (w == 1) v = r_neg<L>(v);
+#pragma unroll
+        for (int l = 0; l < L; l++) ws.part_rcp[(int64_t)q * 2 * L + w * L + l] = v.x[l];
+        __threadfence();
+      }
+      __syncthreads();
+      if (has && tid == 0) st_release(cw.rcp_flag + q, (int)(j + 1));
     }
     if (!coop_wait(cw, gen)) return;
     // 2. reduce the partials (every CTA, same result)
