@@ -133,6 +133,26 @@ int launch_tri_block(dim3 grid, dim3 block, cudaStream_t s, View A, int64_t k0, 
   return 0;
 }
 
+// Unit lower block solve of the bs x bs block of A at (k0, k0) on ncols
+// columns of X (rows xrow0 ..): the four-warp-group kernel where the step
+// chain is latency bound (bs <= 64, or TD/QD up to 128: measured faster),
+// else the one-thread-per-row block solve (DD at 128 rows is bound by each
+// SMSP's FP64 throughput, where the extra barriers cost more).
+template <int L>
+int launch_lsolve(cudaStream_t s, View A, int64_t k0, int bs, View X, int64_t ncols, int64_t xrow0) {
+  if (ncols <= 0) return 0;
+  const int RT = (bs + 31) / 32 * 32;
+  if (bs <= 64 || (L >= 3 && bs <= 128)) {
+    k_lsolve4<L><<<(unsigned)ncols, dim3(RT, 4), lsolve4_smem<L>(RT), s>>>(A, k0, bs, X, xrow0);
+    MCLU_LAUNCHED();
+    return 0;
+  }
+  // one column per CTA: the solve is bound by each SM's FP64 unit, so the
+  // columns go to as many SMs as possible
+  return launch_tri_block<L, true, true, false>(dim3((unsigned)ncols), dim3(RT, 1), s, A, k0, bs, X, ncols, nullptr, 0,
+                                                xrow0);
+}
+
 // Cooperative panel factorisation.  Returns 0 (launched), 1 (the grid or its
 // shared memory does not fit: caller falls back to per-column launches) or a
 // CUDA error code.
@@ -330,8 +350,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
           if (rc) return rc;
           ProfScope ps(PK_OTHER, s);
           View U{Ap + send * lda, lda, lda * n};  // rows s0.., columns send..jend
-          rc = launch_tri_block<L, true, true, false>(dim3((unsigned)(jend - send)), dim3((int)((sb + 31) / 32 * 32), 1),
-                                                      s, A, s0, (int)sb, U, jend - send, nullptr, 0, s0);
+          rc = launch_lsolve<L>(s, A, s0, (int)sb, U, jend - send, s0);
           if (rc) return rc;
           rc = oz::gemm<L>(true, View{Ap + s0 * lda + send, lda, lda * n}, View{Ap + send * lda + s0, lda, lda * n},
                            View{Ap + send * lda + send, lda, lda * n}, n - send, jend - send, sb, oz_ws, oz_status, s,
@@ -348,12 +367,9 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
       const int64_t n2 = n - jend;
       {  // U12 = L11^{-1} A12
         ProfScope ps(PK_TRSM, s);
-        const int RT = (int)((jb + 31) / 32 * 32);
-        const int CT = std::max(1, 256 / RT);
         View A12{Ap + jend * lda, lda, lda * n};
         if (!ozk) {
-          int rc = launch_tri_block<L, true, true, false>(dim3((unsigned)cdiv(n2, CT)), dim3(RT, CT), s, A, j0, (int)jb,
-                                                          A12, n2, nullptr, 0, j0);
+          int rc = launch_lsolve<L>(s, A, j0, (int)jb, A12, n2, j0);
           if (rc) return rc;
         } else {
           // W = L11^{-1} (unit lower, jb x jb) by the same block solve on the
@@ -362,10 +378,9 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
           View W{winv, jb, jb * jb};
           k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(W, jb);
           MCLU_LAUNCHED();
-          // one CTA per column of W: the block solve is FP64-pipe bound per
-          // SM, so the jb columns go to jb SMs
-          int rc0 = launch_tri_block<L, true, true, false>(dim3((unsigned)jb), dim3(RT, 1), s, A, j0, (int)jb, W,
-                                                           jb, nullptr, 0, 0);
+          // one CTA per column of W (the solve is FP64-latency bound, so the
+          // jb columns go to jb SMs)
+          int rc0 = launch_lsolve<L>(s, A, j0, (int)jb, W, jb, 0);
           if (rc0) return rc0;
           int rc = oz::gemm<L>(false, W, View{Ap + jend * lda + j0, lda, lda * n}, View{Ap + jend * lda + j0, lda, lda * n},
                                jb, n2, jb, oz_ws, oz_status, s, note_launch);

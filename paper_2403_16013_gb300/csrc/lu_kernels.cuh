@@ -623,6 +623,94 @@ __global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, c
   if (ok) stz<L>(X, xrow0 + tx, c, x);
 }
 
+// Unit lower triangular solve T x = b for the bs x bs diagonal block of A at
+// (k0, k0) on column blockIdx.x of X (rows xrow0 .. xrow0+bs-1); the
+// diagonal is unit, the strictly lower part is read from A.  Thread (r, p)
+// holds row r's partial accumulator p of the four real products of the
+// complex update x_r -= T(r,k) x_k:
+//   p = 0: Re x - sum Re T Re x     p = 1: + sum Im T Im x
+//   p = 2: Im x - sum Re T Im x     p = 3: - sum Im T Re x
+// so each step costs every SMSP one product (the four warp groups run on
+// four FP64 units), and x_k = (P0 + P1) + i (P2 + P3) is formed when row k
+// is final.  Column k of T is streamed into shared memory one step ahead
+// (double-buffered).  Block (bs rounded up to 32, 4), bs <= 128.
+template <int L>
+__global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, View X, int64_t xrow0) {
+  const int r = threadIdx.x, p = threadIdx.y;
+  const int RT = blockDim.x;
+  const int tid = p * RT + r, nthr = 4 * RT;
+  const int64_t c = blockIdx.x;
+  extern __shared__ double lsm4[];
+  double *col = lsm4;                              // [2][RT][2L]: column k of T
+  double *part = col + (size_t)2 * RT * 2 * L;     // [4][L]: row k's partial accumulators
+  double *xk = part + 4 * L;                       // [2L]: x_k
+  const bool own = r < bs;
+  Acc<L> acc;
+  acc.zero();
+  if (own && (p == 0 || p == 2)) {
+    const Z<L> x = ldz<L>(X, xrow0 + r, c);
+    acc.set(p == 0 ? x.re : x.im);
+  }
+  auto fetch = [&](int k, int buf) {  // column k of T, rows k+1 .. bs-1
+    for (int t = tid; t < bs; t += nthr) {
+      if (t <= k) continue;
+      const Z<L> v = ldz<L>(A, k0 + t, k0 + k);
+      double *d = col + ((size_t)buf * RT + t) * 2 * L;
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        d[q] = v.re.x[q];
+        d[L + q] = v.im.x[q];
+      }
+    }
+  };
+  fetch(0, 0);
+  __syncthreads();
+  for (int k = 0; k < bs; k++) {
+    const int buf = k & 1;
+    if (k + 1 < bs) fetch(k + 1, buf ^ 1);
+    if (r == k) {
+#pragma unroll
+      for (int q = 0; q < L; q++) part[p * L + q] = acc.s[q];
+    }
+    __syncthreads();
+    if (r == 0 && (p == 0 || p == 2)) {  // x_k: Re on (0,0), Im on (0,2)
+      Acc<L> t, o;
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        t.s[q] = part[p * L + q];
+        o.s[q] = part[(p + 1) * L + q];
+      }
+      t.add_acc(o, false);
+      const R<L> v = t.result();
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        xk[(p >> 1) * L + q] = v.x[q];
+        X.p[(int64_t)((p >> 1) * L + q) * X.ps + c * X.ld + xrow0 + k] = v.x[q];
+      }
+    }
+    __syncthreads();
+    if (own && r > k) {
+      const double *d = col + ((size_t)buf * RT + r) * 2 * L;
+      R<L> tv, xv;
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        tv.x[q] = d[(p == 0 || p == 2) ? q : L + q];    // Re T for p = 0, 2; Im T for p = 1, 3
+        xv.x[q] = xk[(p == 0 || p == 1) ? (p == 0 ? q : L + q) : (p == 2 ? L + q : q)];
+      }
+      if (p == 1)
+        acc.template add_prod<false>(tv, xv);
+      else
+        acc.template add_prod<true>(tv, xv);
+    }
+    __syncthreads();
+  }
+}
+
+template <int L>
+constexpr size_t lsolve4_smem(int RT) {
+  return ((size_t)2 * RT * 2 * L + 4 * L + 2 * L) * sizeof(double);
+}
+
 // Shared memory of k_tri_block for block size bs and CT columns.
 template <int L>
 constexpr size_t tri_block_smem(int bs, int CT, bool stage) {
