@@ -1080,6 +1080,70 @@ __device__ __forceinline__ void warp_inv_apply(const Z<L> (&w)[2], const double 
   }
 }
 
+// Critical step of the dataflow substitution, split by product over the four
+// warps of the CTA (one SMSP and FP64 unit each): warp p forms product p of
+// every complex MAC of the step for the rows i = lane / 4 (lanes g = lane % 4
+// take j = g, g + 4), combines its four lanes and leaves the partial
+// accumulator in part[p][i][L].
+//   tile update r -= T x:  p0 -Re T Re x, p1 +Im T Im x, p2 -Re T Im x, p3 -Im T Re x
+//   inverse    x = W r:    p0 +Re W Re r, p1 -Im W Im r, p2 +Re W Im r, p3 +Im W Re r
+template <int L, bool INV>
+__device__ __forceinline__ void warp_part(const Z<L> (&m)[2], const double (*v)[2 * L], double *part, int p, int br,
+                                          int bc, bool tri_lower, bool tri, int lane) {
+  const int i = lane >> 2, g = lane & 3;
+  Acc<L> acc;
+  acc.zero();
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int j = g + 4 * h;
+    if (i < br && j < bc && (!tri || (tri_lower ? j <= i : j >= i))) {
+      const Z<L> vj = lds_z<L>(v[j]);
+      const R<L> &a = (p == 0 || p == 2) ? m[h].re : m[h].im;
+      const R<L> &b = (p == 0 || p == 3) ? vj.re : vj.im;
+      if (INV ? (p == 1) : (p != 1))
+        acc.template add_prod<true>(a, b);
+      else
+        acc.template add_prod<false>(a, b);
+    }
+  }
+#pragma unroll
+  for (int off = 2; off > 0; off >>= 1) {
+    Acc<L> o;
+#pragma unroll
+    for (int q = 0; q < L; q++) o.s[q] = __shfl_down_sync(0xffffffffu, acc.s[q], off, 4);
+    acc.add_acc(o, false);
+  }
+  if (g == 0 && i < br) {
+#pragma unroll
+    for (int q = 0; q < L; q++) part[(p * SOLVE_BS + i) * L + q] = acc.s[q];
+  }
+}
+
+// Warps 0 (real part) and 1 (imaginary part): out[i] = base[i] + P_{2w} +
+// P_{2w+1} for the rows i < br (base omitted when null).
+template <int L>
+__device__ __forceinline__ void combine_parts(const double *part, const double (*base)[2 * L], double (*out)[2 * L],
+                                              int br, int warp, int lane) {
+  if (warp < 2 && lane < br) {
+    Acc<L> t, o;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      t.s[q] = part[((2 * warp) * SOLVE_BS + lane) * L + q];
+      o.s[q] = part[((2 * warp + 1) * SOLVE_BS + lane) * L + q];
+    }
+    t.add_acc(o, false);
+    if (base) {
+      R<L> b;
+#pragma unroll
+      for (int q = 0; q < L; q++) b.x[q] = base[lane][warp * L + q];
+      t.add(b);
+    }
+    const R<L> r = t.result();
+#pragma unroll
+    for (int q = 0; q < L; q++) out[lane][warp * L + q] = r.x[q];
+  }
+}
+
 // Shared memory of k_trsv_flow for nown owned blocks.
 template <int L>
 constexpr size_t trsv_flow_smem(int nown) {
@@ -1136,7 +1200,7 @@ __global__ void __launch_bounds__(FLOW_T) k_trsv_flow(View A, int64_t n, const d
     const bool crit = qn < nblk && qn % G == g;
     TileRegs<L, CONJT> tcrit;
     InvRegs<L, LOWER, CONJT> wcrit;
-    if (crit && warp == 0) {  // operands of step 2, read before the wait
+    if (crit) {  // operands of step 2, read before the wait (every warp)
       tcrit.load(A, blk(qn) * BS, blk(q) * BS, rows(qn), rows(q), lane);
       wcrit.load(wblk(qn), rows(qn), lane);
     }
@@ -1163,14 +1227,19 @@ __global__ void __launch_bounds__(FLOW_T) k_trsv_flow(View A, int64_t n, const d
         xs[par][t % rq][t / rq] = __ldcg(Y.p + (int64_t)(t / rq) * Y.ps + blk(q) * BS + t % rq);
       __syncthreads();
     }
-    // 2. the next step's block first
-    if (crit && warp == 0) {
+    // 2. the next step's block first, its products split over the four warps
+    if (crit) {
+      __shared__ double s_part[4 * SOLVE_BS * L];
       const int i = (qn - g) / G;
-      warp_tile_apply<L>(tcrit.t, xs[par], res[i], rows(qn), rows(q), lane);
-      __syncwarp();
-      warp_inv_apply<L>(wcrit.w, res[i], xs[par ^ 1], rows(qn), lane);
-      __syncwarp();
-      publish(qn, xs[par ^ 1]);
+      warp_part<L, false>(tcrit.t, xs[par], s_part, warp, rows(qn), rows(q), false, false, lane);
+      __syncthreads();
+      combine_parts<L>(s_part, res[i], res[i], rows(qn), warp, lane);
+      __syncthreads();
+      warp_part<L, true>(wcrit.w, res[i], s_part, warp, rows(qn), rows(qn), LOWER, true, lane);
+      __syncthreads();
+      combine_parts<L>(s_part, nullptr, xs[par ^ 1], rows(qn), warp, lane);
+      __syncthreads();
+      if (warp == 0) publish(qn, xs[par ^ 1]);
     }
     // 3. the other owned blocks of later steps
     {
@@ -1178,7 +1247,7 @@ __global__ void __launch_bounds__(FLOW_T) k_trsv_flow(View A, int64_t n, const d
       for (int i = 0; i < nown; i++) {
         const int q2 = g + i * G;
         if (q2 <= q || (crit && q2 == qn)) continue;
-        const int wk = crit ? 1 + k % (FLOW_T / 32 - 1) : k % (FLOW_T / 32);
+        const int wk = k % (FLOW_T / 32);
         k++;
         if (warp != wk) continue;
         TileRegs<L, CONJT> t;
