@@ -343,11 +343,9 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
         const int64_t send = std::min<int64_t>(s0 + oz::NB_MAX, jend), sb = send - s0;
         int rc = panel(s0, send);
         if (rc) return rc;
-        rc = laswp(s0, send, j0, s0, s0, s0);  // the block's earlier columns
+        rc = laswp(s0, send, j0, jend, s0, send);  // the block's other columns, in one launch
         if (rc) return rc;
         if (send < jend) {
-          rc = laswp(s0, send, send, jend, jend, jend);  // the block's later columns
-          if (rc) return rc;
           ProfScope ps(PK_OTHER, s);
           View U{Ap + send * lda, lda, lda * n};  // rows s0.., columns send..jend
           rc = launch_lsolve<L>(s, A, s0, (int)sb, U, jend - send, s0);
