@@ -143,7 +143,7 @@ int launch_lsolve(cudaStream_t s, View A, int64_t k0, int bs, View X, int64_t nc
   if (ncols <= 0) return 0;
   const int RT = (bs + 31) / 32 * 32;
   if (bs <= 64 || (L >= 3 && bs <= 128)) {
-    k_lsolve4<L><<<(unsigned)ncols, dim3(RT, 4), lsolve4_smem<L>(RT), s>>>(A, k0, bs, X, xrow0);
+    k_lsolve4<L><<<(unsigned)ncols, dim3(RT, 4), lsolve4_smem<L>(RT), s>>>(A, k0, bs, X, xrow0, 0);
     MCLU_LAUNCHED();
     return 0;
   }
@@ -250,7 +250,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   Workspace w;
   const size_t oz_need = ozk ? oz::ws_bytes<L>(n, n, nb) : 0;
   const size_t ws_need = getrf_ws_bytes<L>(n, nb, m3) + oz_need +
-                         (ozk ? (((size_t)2 * L * nb * nb * sizeof(double) + 255) & ~(size_t)255) : 0);
+                         (ozk ? (((size_t)2 * 2 * L * nb * nb * sizeof(double) + 255) & ~(size_t)255) : 0);
   char *ws_base = nullptr;
   if (ext_ws) {
     if (ext_bytes < ws_need) return MCLU_ERR_SCRATCH_CAPACITY;
@@ -286,7 +286,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     sumU = cv.take<double>((size_t)n * nb * L);
   }
   void *oz_ws = ozk ? (void *)cv.take<char>(oz_need) : nullptr;
-  double *winv = ozk ? cv.take<double>((size_t)2 * L * nb * nb) : nullptr;
+  double *winv = ozk ? cv.take<double>((size_t)2 * 2 * L * nb * nb) : nullptr;  // L11^-1 and a scratch block
   int *oz_status = ws.zflag + 1;  // spare word of the header block
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
   MCLU_TRY(cudaMemsetAsync(cw.rcp_flag, 0, (size_t)2 * COOP_GMAX * sizeof(int), s));
@@ -376,10 +376,35 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
           View W{winv, jb, jb * jb};
           k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(W, jb);
           MCLU_LAUNCHED();
-          // one CTA per column of W (the solve is FP64-latency bound, so the
-          // jb columns go to jb SMs)
-          int rc0 = launch_lsolve<L>(s, A, j0, (int)jb, W, jb, 0);
-          if (rc0) return rc0;
+          constexpr int SB = oz::NB_MAX;  // 32: the sub-panel width
+          if (jb <= SB || L == 2) {
+            // one CTA per column of W (the solve is FP64-latency bound, so
+            // the jb columns go to jb SMs); for DD this direct solve measured
+            // faster than the composition below (its FP64 chain is short)
+            int rc0 = launch_lsolve<L>(s, A, j0, (int)jb, W, jb, 0);
+            if (rc0) return rc0;
+          } else {
+            // the inverses of the 32 x 32 diagonal blocks in one launch, then
+            // 2 x 2 block inversion upwards: inv([[P, 0], [C, Q]]) has the
+            // lower-left block -inv(Q) C inv(P), two Ozaki products per pair
+            const int nsb = (int)cdiv(jb, SB);
+            k_lsolve4<L><<<dim3(SB, nsb), dim3(SB, 4), lsolve4_smem<L>(SB), s>>>(A, j0, (int)jb, W, 0, SB);
+            MCLU_LAUNCHED();
+            View Tm{winv + (size_t)2 * L * nb * nb, nb, (int64_t)nb * nb};  // scratch for C inv(P)
+            for (int64_t h = SB; h < jb; h *= 2) {
+              for (int64_t a = 0; a + h < jb; a += 2 * h) {
+                const int64_t hb = std::min<int64_t>(h, jb - a - h);  // rows of Q
+                View Cv{Ap + (j0 + a) * lda + (j0 + a + h), lda, lda * n};  // L rows a+h.., columns a..
+                View Pi{W.p + a * W.ld + a, W.ld, W.ps};
+                View Qi{W.p + (a + h) * W.ld + (a + h), W.ld, W.ps};
+                View X21{W.p + a * W.ld + (a + h), W.ld, W.ps};
+                int rc1 = oz::gemm<L>(false, Cv, Pi, Tm, hb, h, h, oz_ws, oz_status, s, note_launch);
+                if (rc1) return rc1;
+                rc1 = oz::gemm<L>(true, Qi, Tm, X21, hb, h, hb, oz_ws, oz_status, s, note_launch);
+                if (rc1) return rc1;
+              }
+            }
+          }
           int rc = oz::gemm<L>(false, W, View{Ap + jend * lda + j0, lda, lda * n}, View{Ap + jend * lda + j0, lda, lda * n},
                                jb, n2, jb, oz_ws, oz_status, s, note_launch);
           if (rc) return rc;

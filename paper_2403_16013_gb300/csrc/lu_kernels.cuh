@@ -634,12 +634,23 @@ __global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, c
 // four FP64 units), and x_k = (P0 + P1) + i (P2 + P3) is formed when row k
 // is final.  Column k of T is streamed into shared memory one step ahead
 // (double-buffered).  Block (bs rounded up to 32, 4), bs <= 128.
+// ystep > 0: the grid's y index selects the diagonal block at offset
+// y ystep of a bs-row block (its rows, its columns of X), bs <= ystep rows
+// each: the diagonal-block inverses of a larger triangle in one launch.
 template <int L>
-__global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, View X, int64_t xrow0) {
+__global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, View X, int64_t xrow0, int ystep) {
   const int r = threadIdx.x, p = threadIdx.y;
   const int RT = blockDim.x;
   const int tid = p * RT + r, nthr = 4 * RT;
-  const int64_t c = blockIdx.x;
+  int64_t c = blockIdx.x;
+  if (ystep > 0) {
+    const int koff = (int)blockIdx.y * ystep;
+    bs = min(ystep, bs - koff);
+    if ((int)blockIdx.x >= bs) return;  // whole CTA: beyond this block's columns
+    k0 += koff;
+    xrow0 += koff;
+    c += koff;
+  }
   extern __shared__ double lsm4[];
   double *col = lsm4;                              // [2][RT][2L]: column k of T
   double *part = col + (size_t)2 * RT * 2 * L;     // [4][L]: row k's partial accumulators
