@@ -17,7 +17,9 @@
 //      reads the winner's row from its slot;
 //   3. the owners swap rows j and p in shared memory, every CTA scales its
 //      rows below j by the winner's reciprocal and applies the rank-1 update
-//      to the remaining panel columns.
+//      to the remaining panel columns.  Updated elements stay in leveled-
+//      accumulator form (no renormalisation) except the next pivot column;
+//      rows are renormalised when written back.
 // Partials and row slots alternate between two buffers by column parity: a
 // buffer is rewritten two columns later, after a barrier that every CTA
 // reaches only once it has finished reading it.
@@ -265,7 +267,21 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       ipiv[j] = (int32_t)(p + 1);
       if (zero && *ws.info == 0) *ws.info = (int)(j + 1);
     }
-    if (zero) {  // nothing to eliminate in this column; no swap
+    if (zero) {  // nothing to eliminate in this column; no swap; the next
+                 // pivot column is renormalised for its keys
+      if (jc + 1 < nb) {
+        for (int rr = tid; rr < nr; rr += COOP_T) {
+          if (rbeg + rr <= j) continue;
+          const Z<L> a = ldp(rr, jc + 1);
+          Acc<L> re, im;
+          re.set(a.re);
+          im.set(a.im);
+          Z<L> z;
+          z.re = re.result();
+          z.im = im.result();
+          stp(rr, jc + 1, z);
+        }
+      }
       __syncthreads();
       continue;
     }
@@ -353,15 +369,41 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
           u.re.x[q] = su[cc * 2 * L + q];
           u.im.x[q] = su[cc * 2 * L + L + q];
         }
-        stp(rr, cc, z_fms<L>(ldp(rr, cc), ldp(rr, jc), u));
+        // the element stays in accumulator form (its levels) between
+        // columns; the next pivot column is renormalised here
+        const Z<L> a = ldp(rr, cc);
+        Acc<L> re, im;
+        re.set(a.re);
+        im.set(a.im);
+        acc_csub<L>(re, im, ldp(rr, jc), u);
+        Z<L> z;
+        if (cc == jc + 1) {
+          z.re = re.result();
+          z.im = im.result();
+        } else {
+#pragma unroll
+          for (int q = 0; q < L; q++) {
+            z.re.x[q] = re.s[q];
+            z.im.x[q] = im.s[q];
+          }
+        }
+        stp(rr, cc, z);
       }
     }
     __syncthreads();
   }
-  // write the owned rows back
+  // write the owned rows back, renormalised (elements that left the active
+  // rows, such as the U part of each pivot row, may still hold accumulator levels)
   for (int t = tid; t < nr * nb; t += COOP_T) {
     const int r = t % nr, c = t / nr;
-    stz<L>(A, rbeg + r, j0 + c, ldp(r, c));
+    const Z<L> a = ldp(r, c);
+    Acc<L> re, im;
+    re.set(a.re);
+    im.set(a.im);
+    Z<L> z;
+    z.re = re.result();
+    z.im = im.result();
+    stz<L>(A, rbeg + r, j0 + c, z);
   }
 }
 
