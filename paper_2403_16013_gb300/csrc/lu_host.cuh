@@ -107,6 +107,7 @@ constexpr size_t getrf_ws_bytes(int64_t n, int nb, bool m3) {
   b += ((2 * COOP_GMAX * 2 * L * nbc * sizeof(double)) + 255) & ~(size_t)255;        // prow
   b += ((2 * 2 * L * nbc * sizeof(double)) + 255) & ~(size_t)255;                    // srow
   b += ((2 * COOP_GMAX * sizeof(int)) + 255) & ~(size_t)255;                          // rcp_flag
+  b += ((2 * COOP_GMAX * COOP_KS * sizeof(double)) + 255) & ~(size_t)255;              // kslot
   if (m3) b += 2 * ((((size_t)n * nb * L * sizeof(double)) + 255) & ~(size_t)255);  // 3M pre-sums
   return b + 1024;
 }
@@ -167,8 +168,8 @@ int launch_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int32_t *ipiv
   int G = (int)std::min<int64_t>({(int64_t)sms, cdiv(m, 8), (int64_t)COOP_GMAX});
   if (G < 1) G = 1;
   const int rpc = (int)cdiv(m, G);
-  // owned rows + pivot row + the multipliers' partial products
-  const size_t smem = (((size_t)rpc + 1) * nb * 2 * L + (size_t)4 * rpc * L) * sizeof(double);
+  // owned rows + the pivot rows of two columns + the multipliers' partial products
+  const size_t smem = (((size_t)rpc + 2) * nb * 2 * L + (size_t)4 * rpc * L) * sizeof(double);
   if (smem > 200 * 1024) return 1;
   if (per_sm < 0) {
     MCLU_TRY(cudaFuncSetAttribute(k_panel_coop<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -274,9 +275,8 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   ws.lbuf = cv.take<double>(2 * 2 * L * (size_t)n);
   ws.lbuf_ld = n;
   CoopWS cw;
-  cw.bar_count = (unsigned *)(hdr + 640);
-  cw.bar_gen = (unsigned *)(hdr + 644);
   cw.status = (int *)(hdr + 648);
+  cw.kslot = cv.take<double>((size_t)2 * COOP_GMAX * COOP_KS);
   cw.prow = cv.take<double>((size_t)2 * COOP_GMAX * 2 * L * nbc);
   cw.srow = cv.take<double>((size_t)2 * 2 * L * nbc);
   cw.rcp_flag = cv.take<int>((size_t)2 * COOP_GMAX);
@@ -290,6 +290,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   int *oz_status = ws.zflag + 1;  // spare word of the header block
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
   MCLU_TRY(cudaMemsetAsync(cw.rcp_flag, 0, (size_t)2 * COOP_GMAX * sizeof(int), s));
+  MCLU_TRY(cudaMemsetAsync(cw.kslot, 0, (size_t)2 * COOP_GMAX * COOP_KS * sizeof(double), s));
   View A{Ap, lda, lda * n};
 
   // panel on rows [p0, n), columns [p0, p1): one cooperative launch, or one
@@ -430,7 +431,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
       if (rc) return rc;
     }
   }
-  // a timed-out tensor-core pipeline or grid barrier is reported through info
+  // a timed-out tensor-core pipeline or panel exchange is reported through info
   k_merge_status<<<1, 1, 0, s>>>(oz_status, ws.info);
   MCLU_LAUNCHED();
   k_merge_status<<<1, 1, 0, s>>>(cw.status, ws.info);

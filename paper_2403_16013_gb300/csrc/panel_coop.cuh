@@ -4,27 +4,31 @@
 // One cooperative launch factors the whole panel rows [j0, n) x columns
 // [j0, jend): each CTA keeps a contiguous block of panel rows in shared
 // memory for all nb columns, so a column step needs no kernel launch and no
-// global-memory traffic except the pivot exchange.  Per column j, with one
-// grid barrier:
-//   1. every CTA computes cabs1 keys of its rows i >= j; its best (key, row)
-//      goes to a global partial, its best row (all nb columns) to a global
-//      row slot, and the owner of row j also publishes row j; the CTA then
-//      arrives at the grid barrier and, while the others arrive, computes the
-//      reciprocal of its best value and publishes it with a release flag
-//      stamped with the column;                                -> grid barrier
-//   2. every CTA reduces all partials (same winner p everywhere; ties to the
-//      lowest row), waits for the winner's reciprocal flag (bounded) and
-//      reads the winner's row from its slot;
-//   3. the owners swap rows j and p in shared memory, every CTA scales its
-//      rows below j by the winner's reciprocal and applies the rank-1 update
-//      to the remaining panel columns.  Updated elements stay in leveled-
-//      accumulator form (no renormalisation) except the next pivot column;
-//      rows are renormalised when written back.
-// Partials and row slots alternate between two buffers by column parity: a
-// buffer is rewritten two columns later, after a barrier that every CTA
-// reaches only once it has finished reading it.
-// Grid barriers are counter + generation in global memory with a bounded
-// spin (clock64 budget); a timeout sets *status and every CTA returns.
+// global-memory traffic except the pivot exchange.  Per column j:
+//   1. every CTA computes cabs1 keys of its rows i >= j (column j is up to
+//      date) and writes its best (key, row) to its key slot with a release
+//      stamp (the column);
+//   2. it then applies the pending rank-1 update of column j-1 to the
+//      columns after j (one step of lookahead: only column j was updated
+//      before the keys), first to its best row and to row j, which it
+//      publishes (all nb columns) together with the reciprocal of its best
+//      value under a release flag stamped with the column, then to its other
+//      rows;
+//   3. meanwhile warp 0 reads every CTA's key slot (bounded waits on the
+//      stamps; same winner p everywhere, ties to the lowest row), waits for
+//      the winner's flag, stages its row and swaps rows j and p where this
+//      CTA owns them (both were published rows, so the update of step 2
+//      never touches them);
+//   4. every CTA scales its rows below j by the winner's reciprocal (the
+//      multipliers) and updates column j+1 of those rows, renormalised for
+//      the next keys; the other columns wait for step 2 of the next column.
+// Updated elements stay in leveled-accumulator form (no renormalisation)
+// except the next pivot column; rows are renormalised when written back.
+// Slots, row buffers and pivot rows alternate between two buffers by column
+// parity: a CTA rewrites a buffer two columns later, once every CTA has
+// stamped the column in between, which each does only after reading it.
+// Every wait is bounded (clock64 budget); a timeout sets *status and every
+// CTA returns.
 #pragma once
 
 #include "lu_kernels.cuh"
@@ -34,105 +38,55 @@ namespace mclu {
 constexpr int COOP_T = 256;
 constexpr int COOP_GMAX = 256;                  // most CTAs of one cooperative panel launch
 constexpr long long COOP_WAIT = 2000000000LL;  // ~1 s at 2 GHz
+constexpr int COOP_KS = 16;                     // doubles per key slot (one 128-byte line)
 
 struct CoopWS {
-  unsigned *bar_count;  // arrival counter
-  unsigned *bar_gen;    // generation
-  int *status;          // nonzero: a barrier timed out
-  double *prow;         // [2][G][nb][2L] best row of each CTA, by column parity
-  double *srow;         // [2][nb][2L] row j, by column parity
-  int *rcp_flag;        // [2G] column stamp (j + 1) of the reciprocal in each partial slot
+  int *status;    // nonzero: a wait timed out
+  double *kslot;  // [2][G][COOP_KS]: key (L doubles), then row and stamp (two ints), by column parity
+  double *prow;   // [2][G][nb][2L] best row of each CTA, by column parity
+  double *srow;   // [2][nb][2L] row j, by column parity
+  int *rcp_flag;  // [2G] column stamp (j + 1) of the reciprocal and rows of each slot
 };
 
-// Split grid barrier: arrive returns the generation to wait for; wait spins
-// (bounded) until it has passed.  Returns false on timeout.
-__device__ __forceinline__ unsigned coop_arrive(const CoopWS &cw, unsigned nblocks) {
-  __shared__ unsigned s_gen;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *gen = cw.bar_gen;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(cw.bar_count, 1u) == nblocks - 1) {
-      *cw.bar_count = 0;
-      __threadfence();
-      atomicAdd(cw.bar_gen, 1u);
-    }
-    s_gen = g;
-  }
-  __syncthreads();
-  return s_gen;
+// Barrier over the `count` threads (whole warps) that execute it with this id
+// (id 0 is __syncthreads).
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ bool coop_wait(const CoopWS &cw, unsigned g) {
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned *gen = cw.bar_gen;
-    const long long t0 = clock64();
-    while (*gen == g) {
-      if (clock64() - t0 > COOP_WAIT) {
-        ok = 0;
-        atomicOr(cw.status, 1);
-        break;
-      }
-    }
-    __threadfence();
-    s_ok = ok && (*(volatile int *)cw.status == 0);
-  }
-  __syncthreads();
-  return s_ok != 0;
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
-// Sense-reversal grid barrier with a bounded wait.  Returns false on timeout.
-__device__ __forceinline__ bool coop_barrier(const CoopWS &cw, unsigned nblocks) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned *gen = cw.bar_gen;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(cw.bar_count, 1u) == nblocks - 1) {
-      *cw.bar_count = 0;
-      __threadfence();
-      atomicAdd(cw.bar_gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*gen == g) {
-        if (clock64() - t0 > COOP_WAIT) {
-          ok = 0;
-          atomicOr(cw.status, 1);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = ok && (*(volatile int *)cw.status == 0);
-  }
-  __syncthreads();
-  return s_ok != 0;
+// Bounded wait until *flag == v; false on timeout.
+__device__ __forceinline__ bool coop_wait_flag(const int *flag, int v) {
+  const long long t0 = clock64();
+  while (ld_acquire(flag) != v)
+    if (clock64() - t0 > COOP_WAIT) return false;
+  return true;
 }
 
 // Factor panel columns [j0, jend) of rows [j0, n).  CTA b owns rows
 // [j0 + b*rpc, j0 + min((b+1)*rpc, n - j0)).  Shared memory: the owned rows,
 // [col][component][row] with the row fastest (consecutive threads take
-// consecutive rows: no bank conflicts), then the pivot row of the current
-// column [col][component], then the multipliers' four partial products
-// [4][row][L].  Partial slots: par * G + b for column parity par.
+// consecutive rows: no bank conflicts), then the pivot rows of the two column
+// parities [col][component], then the multipliers' four partial products
+// [4][row][L].  Slot of this CTA for column parity par: par * G + b.
 template <int L>
 __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int rpc,
                                                       int32_t *ipiv, PanelWS<L> ws, CoopWS cw) {
   extern __shared__ double sp[];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int nb = (int)(jend - j0);
   const int G = (int)gridDim.x, b = (int)blockIdx.x;
   const int64_t rbeg = j0 + (int64_t)b * rpc;
   const int64_t rend = min(n, rbeg + rpc);
   const int nr = (int)max((int64_t)0, rend - rbeg);
-  const int RW = nb * 2 * L;  // doubles per panel row
-  double *su = sp + (size_t)rpc * RW;  // pivot row [col][2L]
-  double *mscr = su + RW;              // [4][rpc][L] the multipliers' partial products
+  const int RW = nb * 2 * L;             // doubles per panel row
+  double *su2 = sp + (size_t)rpc * RW;   // pivot rows [2][col][2L]
+  double *mscr = su2 + 2 * (size_t)RW;   // [4][rpc][L] the multipliers' partial products
   auto ldp = [&](int r, int c) {
     Z<L> z;
     const double *d = sp + (size_t)c * 2 * L * rpc + r;
@@ -153,56 +107,93 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
   };
   // element t = c * 2L + q of row r (the global row-slot format)
   auto rowel = [&](int r, int t) -> double & { return sp[(size_t)t * rpc + r]; };
+  // element (r, c) minus l u, l = column jm of row r, u = element c of the
+  // pivot row su; the result stays in accumulator form (its levels)
+  auto upd = [&](int r, int c, int jm, const double *su) {
+    Z<L> u;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      u.re.x[q] = su[c * 2 * L + q];
+      u.im.x[q] = su[c * 2 * L + L + q];
+    }
+    const Z<L> a = ldp(r, c);
+    Acc<L> re, im;
+    re.set(a.re);
+    im.set(a.im);
+    acc_csub<L>(re, im, ldp(r, jm), u);
+    Z<L> z;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      z.re.x[q] = re.s[q];
+      z.im.x[q] = im.s[q];
+    }
+    return z;
+  };
   // load the owned rows
   for (int t = tid; t < nr * nb; t += COOP_T) {
     const int r = t % nr, c = t / nr;
     stp(r, c, ldz<L>(A, rbeg + r, j0 + c));
   }
+  __shared__ int s_zero, s_next, s_pend, s_ok, s_cand;
+  __shared__ double s_rcp[2 * L];
+  if (tid == 0) {
+    s_next = 0;
+    s_pend = 0;
+    s_ok = 1;
+  }
   __syncthreads();
-  __shared__ int s_p, s_zero, s_part;
   for (int jc = 0; jc < nb; jc++) {
     const int64_t j = j0 + jc;
     const int par = jc & 1;
-    // 1. keys of the rows i >= j of this CTA
-    R<L> key = invalid_key<L>();
-    int idx = INT_MAX;
-    for (int r = tid; r < nr; r += COOP_T) {
-      const int64_t i = rbeg + r;
-      if (i < j) continue;
-      const R<L> k = pivot_key<L>(ldp(r, jc));
-      if (better<L>(k, (int)i, key, idx)) {
-        key = k;
-        idx = (int)i;
-      }
-    }
-    const int cand = write_partial_key<L>(key, idx, ws, par * G + b, tid, COOP_T);
-    // publish this CTA's best row and, from its owner, row j
-    if (cand != INT_MAX) {
-      double *dst = cw.prow + ((size_t)par * G + b) * RW;
-      const int r = (int)(cand - rbeg);
-      for (int t = tid; t < RW; t += COOP_T) dst[t] = rowel(r, t);
-    }
-    if (j >= rbeg && j < rend) {
-      double *dst = cw.srow + (size_t)par * RW;
-      const int r = (int)(j - rbeg);
-      for (int t = tid; t < RW; t += COOP_T) dst[t] = rowel(r, t);
-    }
-    const unsigned gen = coop_arrive(cw, G);
-    // the reciprocal 1/p = conj(p) / |p|^2 of this CTA's candidate, while the
-    // other CTAs arrive, split over warps 0 and 1 (two SMSPs, two FP64
-    // units): Re p^2 and Im p^2 in parallel, the real reciprocal x of |p|^2
-    // on warp 0, then Re p x and -Im p x in parallel; published with a
-    // release flag stamped with the column
+    double *su = su2 + (size_t)par * RW;                 // pivot row of column jc
+    const double *sprev = su2 + (size_t)(par ^ 1) * RW;  // pivot row of column jc - 1
+    const bool pend = s_pend != 0;  // the update of columns jc+1.. from column jc-1 is pending
+    const int q = par * G + b;
+    // 1. keys of the rows i >= j of this CTA; its best goes to its key slot
     {
+      R<L> key = invalid_key<L>();
+      int idx = INT_MAX;
+      for (int r = tid; r < nr; r += COOP_T) {
+        const int64_t i = rbeg + r;
+        if (i < j) continue;
+        const R<L> k = pivot_key<L>(ldp(r, jc));
+        if (better<L>(k, (int)i, key, idx)) {
+          key = k;
+          idx = (int)i;
+        }
+      }
+      block_argmax<L>(key, idx, tid, COOP_T);
+      if (tid == 0) {
+        double *slot = cw.kslot + (size_t)q * COOP_KS;
+#pragma unroll
+        for (int l = 0; l < L; l++) slot[l] = key.x[l];
+        int *si = (int *)(slot + L);
+        si[0] = idx;
+        st_release(si + 1, (int)(j + 1));
+        s_cand = idx;
+      }
+      __syncthreads();
+    }
+    const int cand = s_cand;
+    const bool has = cand != INT_MAX;                                // uniform over the CTA
+    const int cr = has ? (int)(cand - rbeg) : -1;                    // local row of the candidate
+    const int jr = (j >= rbeg && j < rend) ? (int)(j - rbeg) : -1;  // local row j
+    // 2. warps 0 and 1: the reciprocal 1/p = conj(p) / |p|^2 of the
+    //    candidate (SMSPs 0 and 1: Re p^2 and Im p^2 in parallel, the real
+    //    reciprocal x of |p|^2 on warp 0, then Re p x and -Im p x in
+    //    parallel; warps 4 and 5 keep off those two FP64 units meanwhile);
+    //    warps 2 and 3: the pending update of the candidate row and of row j,
+    //    published to their slots; once both are done thread 0 releases the
+    //    flag.  The rest of the pending update goes in 32-element pieces to
+    //    whole warps: 6 and 7 at once, the others when free (warp 0 does
+    //    step 3 instead).
+    if ((w & 2) == 0) {
       __shared__ double s_inv[2 * L];  // Im p^2 accumulator, then x
-      const int w = tid >> 5, lane = tid & 31;
-      const bool has = cand != INT_MAX;  // uniform over the CTA
       const bool act = has && lane == 0 && w < 2;
-      const int q = par * G + b;
       Z<L> pv;
       Acc<L> t;
       if (act) {
-        pv = ldp((int)(cand - rbeg), jc);
+        pv = ldp(cr, jc);
         const R<L> h = w == 0 ? pv.re : pv.im;
         t.set_prod(h, h);
         if (w == 1) {
@@ -210,7 +201,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
           for (int l = 0; l < L; l++) s_inv[l] = t.s[l];
         }
       }
-      __syncthreads();
+      named_sync(1, 128);
       if (has && tid == 0) {
         Acc<L> o;
 #pragma unroll
@@ -220,7 +211,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
 #pragma unroll
         for (int l = 0; l < L; l++) s_inv[L + l] = x.x[l];
       }
-      __syncthreads();
+      named_sync(1, 128);
       if (act) {
         R<L> x;
 #pragma unroll
@@ -229,46 +220,155 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         if (w == 1) v = r_neg<L>(v);
 #pragma unroll
         for (int l = 0; l < L; l++) ws.part_rcp[(int64_t)q * 2 * L + w * L + l] = v.x[l];
-        __threadfence();
       }
-      __syncthreads();
-      if (has && tid == 0) st_release(cw.rcp_flag + q, (int)(j + 1));
-    }
-    if (!coop_wait(cw, gen)) return;
-    // 2. reduce the partials (every CTA, same result)
-    {
-      R<L> bk = invalid_key<L>();
-      int bi = INT_MAX, bq = -1;
-      for (int q = par * G + tid; q < par * G + G; q += COOP_T) {
-        R<L> k;
+    } else if (w < 4) {
+      // warp 2: the candidate row (and the row-j slot when it is row j);
+      // warp 3: row j when it is another row of this CTA
+      const int r = w == 2 ? cr : (jr != cr ? jr : -1);
+      if (r >= 0) {
+        double *dst = w == 2 ? cw.prow + (size_t)q * RW : cw.srow + (size_t)par * RW;
+        double *dst2 = (w == 2 && jr == cr) ? cw.srow + (size_t)par * RW : nullptr;
+        for (int c = lane; c < nb; c += 32) {
+          Z<L> z;
+          if (pend && c > jc) {
+            z = upd(r, c, jc - 1, sprev);
+            stp(r, c, z);
+          } else {
+            z = ldp(r, c);
+          }
 #pragma unroll
-        for (int l = 0; l < L; l++) k.x[l] = __ldcg(ws.part_key + (int64_t)q * L + l);
-        const int i = __ldcg(ws.part_idx + q);
-        if (better<L>(k, i, bk, bi)) {
-          bk = k;
-          bi = i;
-          bq = q;
+          for (int l = 0; l < L; l++) {
+            dst[c * 2 * L + l] = z.re.x[l];
+            dst[c * 2 * L + L + l] = z.im.x[l];
+          }
+          if (dst2) {
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+              dst2[c * 2 * L + l] = z.re.x[l];
+              dst2[c * 2 * L + L + l] = z.im.x[l];
+            }
+          }
         }
       }
-      const int my = bi;
-      block_argmax<L>(bk, bi, tid, COOP_T);
-      if (tid == 0) {
-        const bool zero = !(bk.x[0] > 0.0);
-        s_p = (bi == INT_MAX || zero) ? (int)j : bi;
-        s_zero = zero ? 1 : 0;
+    }
+    if (w < 4) {
+      named_sync(2, 128);
+      if (has && tid == 0) {
+        __threadfence();
+        st_release(cw.rcp_flag + q, (int)(j + 1));
       }
-      __syncthreads();
-      if (my == s_p && my != INT_MAX && !s_zero) s_part = bq;
-      __syncthreads();
     }
-    const int64_t p = s_p;
-    const bool zero = s_zero != 0;
-    if (b == 0 && tid == 0) {
-      ipiv[j] = (int32_t)(p + 1);
-      if (zero && *ws.info == 0) *ws.info = (int)(j + 1);
+    if (w == 0) {
+      // 3. the winner over all key slots of this column: lane l takes slots
+      //    l, l + 32, ...; their stamps are read together (relaxed) until
+      //    all carry the column, then one fence orders the key reads after
+      //    them (an acquire pattern), and the keys are read together
+      constexpr int KMAX = COOP_GMAX / 32;
+      unsigned pendk = 0;
+#pragma unroll
+      for (int k = 0; k < KMAX; k++)
+        if (lane + 32 * k < G) pendk |= 1u << k;
+      bool ok = true;
+      const long long t0 = clock64();
+      while (pendk) {
+        unsigned still = 0;
+#pragma unroll
+        for (int k = 0; k < KMAX; k++)
+          if ((pendk >> k) & 1u) {
+            const double *slot = cw.kslot + ((size_t)par * G + lane + 32 * k) * COOP_KS;
+            if (ld_relaxed((const int *)(slot + L) + 1) != (int)(j + 1)) still |= 1u << k;
+          }
+        pendk = still;
+        if (pendk && clock64() - t0 > COOP_WAIT) {
+          ok = false;
+          break;
+        }
+      }
+      __threadfence();
+      R<L> bk = invalid_key<L>();
+      int bi = INT_MAX, bq = -1;
+      // keys in batches of KB slots per lane (registers)
+      constexpr int KB = L == 2 ? KMAX : KMAX / 2;
+#pragma unroll
+      for (int k0 = 0; k0 < KMAX; k0 += KB) {
+        if (!ok || lane + 32 * k0 >= G) break;
+        R<L> kk[KB];
+        int ki[KB];
+#pragma unroll
+        for (int k = 0; k < KB; k++) {
+          ki[k] = INT_MAX;
+          if (lane + 32 * (k0 + k) < G) {
+            const double *slot = cw.kslot + ((size_t)par * G + lane + 32 * (k0 + k)) * COOP_KS;
+#pragma unroll
+            for (int l = 0; l < L; l++) kk[k].x[l] = __ldcg(slot + l);
+            ki[k] = __ldcg((const int *)(slot + L));
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < KB; k++)
+          if (lane + 32 * (k0 + k) < G && better<L>(kk[k], ki[k], bk, bi)) {
+            bk = kk[k];
+            bi = ki[k];
+            bq = par * G + lane + 32 * (k0 + k);
+          }
+      }
+      ok = __all_sync(0xffffffffu, ok);
+      const int my = bi, myq = bq;
+      if (ok) warp_argmax<L>(bk, bi);
+      const bool zero = !(bk.x[0] > 0.0);
+      const int64_t p = (bi == INT_MAX || zero) ? j : bi;
+      const unsigned own = __ballot_sync(0xffffffffu, my == bi && my != INT_MAX);
+      const int part = own ? __shfl_sync(0xffffffffu, myq, __ffs(own) - 1) : -1;
+      const bool own_p = p != j && p >= rbeg && p < rend;
+      if (ok && !zero && lane == 0) {
+        // the winner's reciprocal and row; row j where this CTA owns row p
+        ok = coop_wait_flag(cw.rcp_flag + part, (int)(j + 1)) &&
+             (!own_p || coop_wait_flag(cw.rcp_flag + par * G + (int)((j - j0) / rpc), (int)(j + 1)));
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (ok && !zero) {
+        const double *prow = cw.prow + (size_t)part * RW;
+        for (int t = lane; t < RW; t += 32) su[t] = __ldcg(prow + t);
+        if (lane < 2 * L) s_rcp[lane] = __ldcg(ws.part_rcp + (int64_t)part * 2 * L + lane);
+        __syncwarp();
+        if (own_p) {
+          const double *srow = cw.srow + (size_t)par * RW;
+          for (int t = lane; t < RW; t += 32) rowel((int)(p - rbeg), t) = __ldcg(srow + t);
+        }
+        if (p != j && jr >= 0)
+          for (int t = lane; t < RW; t += 32) rowel(jr, t) = su[t];
+      }
+      if (lane == 0) {
+        if (!ok) {
+          atomicOr(cw.status, 1);
+          s_ok = 0;
+        }
+        s_zero = zero ? 1 : 0;
+        if (ok && b == 0) {
+          ipiv[j] = (int32_t)(p + 1);
+          if (zero && *ws.info == 0) *ws.info = (int)(j + 1);
+        }
+      }
+    } else if (pend) {
+      const int rlo = (int)max((int64_t)0, j - rbeg);  // rows i > j - 1
+      const int nrow = nr - rlo, ncol = nb - jc - 1;
+      const int tot = nrow > 0 ? nrow * ncol : 0;
+      for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&s_next, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= tot) break;
+        const int t = base + lane;
+        if (t < tot) {
+          const int rr = rlo + t % nrow, cc = jc + 1 + t / nrow;
+          if (rr != cr && rr != jr) stp(rr, cc, upd(rr, cc, jc - 1, sprev));
+        }
+      }
     }
-    if (zero) {  // nothing to eliminate in this column; no swap; the next
-                 // pivot column is renormalised for its keys
+    __syncthreads();
+    if (!s_ok) return;
+    if (s_zero) {  // nothing to eliminate in this column; no swap; the next
+                   // pivot column is renormalised for its keys
       if (jc + 1 < nb) {
         for (int rr = tid; rr < nr; rr += COOP_T) {
           if (rbeg + rr <= j) continue;
@@ -282,112 +382,96 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
           stp(rr, jc + 1, z);
         }
       }
+      if (tid == 0) {
+        s_pend = 0;
+        s_next = 0;
+      }
       __syncthreads();
       continue;
     }
-    // 3. wait for the winner's reciprocal (bounded), stage the pivot row
-    //    (row p before the swap), swap, scale, update
-    {
-      __shared__ int s_rok;
-      if (tid == 0) {
-        int ok = 1;
-        const long long t0 = clock64();
-        while (ld_acquire(cw.rcp_flag + s_part) != (int)(j + 1)) {
-          if (clock64() - t0 > COOP_WAIT) {
-            ok = 0;
-            atomicOr(cw.status, 1);
-            break;
-          }
-        }
-        s_rok = ok;
-      }
-      __syncthreads();
-      if (!s_rok) return;
-    }
-    const double *prow = cw.prow + (size_t)s_part * RW;
-    for (int t = tid; t < RW; t += COOP_T) su[t] = __ldcg(prow + t);
-    __syncthreads();
-    if (p != j) {
-      const double *srow = cw.srow + (size_t)par * RW;
-      if (p >= rbeg && p < rend)
-        for (int t = tid; t < RW; t += COOP_T) rowel((int)(p - rbeg), t) = __ldcg(srow + t);
-      if (j >= rbeg && j < rend)
-        for (int t = tid; t < RW; t += COOP_T) rowel((int)(j - rbeg), t) = su[t];
-    }
-    __syncthreads();
     {
       Z<L> r;
 #pragma unroll
-      for (int q = 0; q < L; q++) {
-        r.re.x[q] = __ldcg(ws.part_rcp + (int64_t)s_part * 2 * L + q);
-        r.im.x[q] = __ldcg(ws.part_rcp + (int64_t)s_part * 2 * L + L + q);
+      for (int l = 0; l < L; l++) {
+        r.re.x[l] = s_rcp[l];
+        r.im.x[l] = s_rcp[L + l];
       }
-      // multipliers l = a r of the rows below j: warps 0..3 (one per SMSP,
-      // each with its own FP64 unit) form the four real products
-      // Re a Re r, Im a Im r, Re a Im r, Im a Re r on leveled accumulators;
-      // warps 0 and 1 then form Re l = P0 - P1 and Im l = P2 + P3
-      {
-        const int w = tid >> 5, lane = tid & 31;
+      // 4. multipliers l = a r of the rows below j: warps 0..3 (one per
+      //    SMSP, each with its own FP64 unit) form the four real products
+      //    Re a Re r, Im a Im r, Re a Im r, Im a Re r on leveled
+      //    accumulators; warps 0 and 1 then form Re l = P0 - P1 and
+      //    Im l = P2 + P3
+      if (w < 4) {
+        const R<L> y = (w == 0 || w == 3) ? r.re : r.im;
+        for (int rr = lane; rr < nr; rr += 32) {
+          if (rbeg + rr <= j) continue;
+          const Z<L> a = ldp(rr, jc);
+          Acc<L> t;
+          t.set_prod((w == 0 || w == 2) ? a.re : a.im, y);
+#pragma unroll
+          for (int l = 0; l < L; l++) mscr[((size_t)w * rpc + rr) * L + l] = t.s[l];
+        }
+      }
+      __syncthreads();
+      if (w < 2) {
+        for (int rr = lane; rr < nr; rr += 32) {
+          if (rbeg + rr <= j) continue;
+          Acc<L> t, o;
+#pragma unroll
+          for (int l = 0; l < L; l++) {
+            t.s[l] = mscr[((size_t)(2 * w) * rpc + rr) * L + l];
+            o.s[l] = mscr[((size_t)(2 * w + 1) * rpc + rr) * L + l];
+          }
+          t.add_acc(o, w == 0);
+          const R<L> v = t.result();
+          double *d = sp + (size_t)jc * 2 * L * rpc + rr + (size_t)(w * L) * rpc;
+#pragma unroll
+          for (int l = 0; l < L; l++) d[(size_t)l * rpc] = v.x[l];
+        }
+      }
+      __syncthreads();
+      // the next pivot column jc+1 now, renormalised for its keys (the
+      // columns after it wait for the next column's step 2), split like the
+      // multipliers: warps 0..3 form Re l Re u, Im l Im u, Re l Im u,
+      // Im l Re u; warps 0 and 1 take a - P0 + P1 and a - P2 - P3
+      if (jc + 1 < nb) {
+        const int cc = jc + 1;
         if (w < 4) {
-          const R<L> y = (w == 0 || w == 3) ? r.re : r.im;
+          R<L> y;
+#pragma unroll
+          for (int l = 0; l < L; l++) y.x[l] = su[cc * 2 * L + ((w == 0 || w == 3) ? 0 : L) + l];
           for (int rr = lane; rr < nr; rr += 32) {
             if (rbeg + rr <= j) continue;
-            const Z<L> a = ldp(rr, jc);
+            const Z<L> lv = ldp(rr, jc);
             Acc<L> t;
-            t.set_prod((w == 0 || w == 2) ? a.re : a.im, y);
+            t.set_prod((w == 0 || w == 2) ? lv.re : lv.im, y);
 #pragma unroll
-            for (int q = 0; q < L; q++) mscr[((size_t)w * rpc + rr) * L + q] = t.s[q];
+            for (int l = 0; l < L; l++) mscr[((size_t)w * rpc + rr) * L + l] = t.s[l];
           }
         }
         __syncthreads();
         if (w < 2) {
           for (int rr = lane; rr < nr; rr += 32) {
             if (rbeg + rr <= j) continue;
+            const Z<L> a = ldp(rr, cc);
             Acc<L> t, o;
+            t.set(w == 0 ? a.re : a.im);
 #pragma unroll
-            for (int q = 0; q < L; q++) {
-              t.s[q] = mscr[((size_t)(2 * w) * rpc + rr) * L + q];
-              o.s[q] = mscr[((size_t)(2 * w + 1) * rpc + rr) * L + q];
-            }
-            t.add_acc(o, w == 0);
+            for (int l = 0; l < L; l++) o.s[l] = mscr[((size_t)(2 * w) * rpc + rr) * L + l];
+            t.add_acc(o, true);
+#pragma unroll
+            for (int l = 0; l < L; l++) o.s[l] = mscr[((size_t)(2 * w + 1) * rpc + rr) * L + l];
+            t.add_acc(o, w == 1);
             const R<L> v = t.result();
-            double *d = sp + (size_t)jc * 2 * L * rpc + rr + (size_t)(w * L) * rpc;
+            double *d = sp + (size_t)cc * 2 * L * rpc + rr + (size_t)(w * L) * rpc;
 #pragma unroll
-            for (int q = 0; q < L; q++) d[(size_t)q * rpc] = v.x[q];
+            for (int l = 0; l < L; l++) d[(size_t)l * rpc] = v.x[l];
           }
         }
       }
-      __syncthreads();
-      // rank-1 update of columns jc+1 .. nb-1 with the staged pivot row
-      const int ncol = nb - jc - 1;
-      for (int t = tid; t < nr * ncol; t += COOP_T) {
-        const int rr = t % nr, cc = jc + 1 + t / nr;
-        if (rbeg + rr <= j) continue;
-        Z<L> u;
-#pragma unroll
-        for (int q = 0; q < L; q++) {
-          u.re.x[q] = su[cc * 2 * L + q];
-          u.im.x[q] = su[cc * 2 * L + L + q];
-        }
-        // the element stays in accumulator form (its levels) between
-        // columns; the next pivot column is renormalised here
-        const Z<L> a = ldp(rr, cc);
-        Acc<L> re, im;
-        re.set(a.re);
-        im.set(a.im);
-        acc_csub<L>(re, im, ldp(rr, jc), u);
-        Z<L> z;
-        if (cc == jc + 1) {
-          z.re = re.result();
-          z.im = im.result();
-        } else {
-#pragma unroll
-          for (int q = 0; q < L; q++) {
-            z.re.x[q] = re.s[q];
-            z.im.x[q] = im.s[q];
-          }
-        }
-        stp(rr, cc, z);
+      if (tid == 0) {
+        s_pend = jc + 2 < nb ? 1 : 0;
+        s_next = 0;
       }
     }
     __syncthreads();
