@@ -14,7 +14,7 @@
 //      publishes (all nb columns) together with the reciprocal of its best
 //      value under a release flag stamped with the column, then to its other
 //      rows;
-//   3. meanwhile warp 0 reads every CTA's key slot (bounded waits on the
+//   3. meanwhile one warp reads every CTA's key slot (bounded waits on the
 //      stamps; same winner p everywhere, ties to the lowest row), waits for
 //      the winner's flag, stages its row and swaps rows j and p where this
 //      CTA owns them (both were published rows, so the update of step 2
@@ -52,6 +52,10 @@ struct CoopWS {
 // (id 0 is __syncthreads).
 __device__ __forceinline__ void named_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// Arrive at that barrier without waiting (the producers of a bar.sync).
+__device__ __forceinline__ void named_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 __device__ __forceinline__ int ld_relaxed(const int *p) {
@@ -182,11 +186,11 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     //    candidate (SMSPs 0 and 1: Re p^2 and Im p^2 in parallel, the real
     //    reciprocal x of |p|^2 on warp 0, then Re p x and -Im p x in
     //    parallel; warps 4 and 5 keep off those two FP64 units meanwhile);
-    //    warps 2 and 3: the pending update of the candidate row and of row j,
-    //    published to their slots; once both are done thread 0 releases the
-    //    flag.  The rest of the pending update goes in 32-element pieces to
-    //    whole warps: 6 and 7 at once, the others when free (warp 0 does
-    //    step 3 instead).
+    //    warps 2 and 6: the pending update of the candidate row and of row j,
+    //    published to their slots; once all four are done thread 0 releases
+    //    the flag.  Warp 3 does step 3 at the same time (it needs no FP64
+    //    unit until the swap).  The rest of the pending update goes in
+    //    32-element pieces to whole warps: 7 at once, the others when free.
     if ((w & 2) == 0) {
       __shared__ double s_inv[2 * L];  // Im p^2 accumulator, then x
       const bool act = has && lane == 0 && w < 2;
@@ -221,9 +225,9 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
 #pragma unroll
         for (int l = 0; l < L; l++) ws.part_rcp[(int64_t)q * 2 * L + w * L + l] = v.x[l];
       }
-    } else if (w < 4) {
+    } else if (w == 2 || w == 6) {
       // warp 2: the candidate row (and the row-j slot when it is row j);
-      // warp 3: row j when it is another row of this CTA
+      // warp 6: row j when it is another row of this CTA
       const int r = w == 2 ? cr : (jr != cr ? jr : -1);
       if (r >= 0) {
         double *dst = w == 2 ? cw.prow + (size_t)q * RW : cw.srow + (size_t)par * RW;
@@ -250,15 +254,16 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
           }
         }
       }
+      named_arrive(3, 96);  // rows cr and jr are final: warp 3 may swap them
     }
-    if (w < 4) {
+    if (w == 0 || w == 1 || w == 2 || w == 6) {
       named_sync(2, 128);
       if (has && tid == 0) {
         __threadfence();
         st_release(cw.rcp_flag + q, (int)(j + 1));
       }
     }
-    if (w == 0) {
+    if (w == 3) {
       // 3. the winner over all key slots of this column: lane l takes slots
       //    l, l + 32, ...; their stamps are read together (relaxed) until
       //    all carry the column, then one fence orders the key reads after
@@ -330,7 +335,9 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         const double *prow = cw.prow + (size_t)part * RW;
         for (int t = lane; t < RW; t += 32) su[t] = __ldcg(prow + t);
         if (lane < 2 * L) s_rcp[lane] = __ldcg(ws.part_rcp + (int64_t)part * 2 * L + lane);
-        __syncwarp();
+      }
+      named_sync(3, 96);  // warps 2 and 6 are done with rows cr and jr
+      if (ok && !zero) {
         if (own_p) {
           const double *srow = cw.srow + (size_t)par * RW;
           for (int t = lane; t < RW; t += 32) rowel((int)(p - rbeg), t) = __ldcg(srow + t);
