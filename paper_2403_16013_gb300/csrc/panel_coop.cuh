@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     stp(r, c, ldz<L>(A, rbeg + r, j0 + c));
   }
   __shared__ int s_zero, s_next, s_pend, s_ok, s_cand;
-  __shared__ double s_rcp[2 * L];
+  __shared__ double s_rcp[2 * L], s_key[L];
   if (tid == 0) {
     s_next = 0;
     s_pend = 0;
@@ -168,12 +168,8 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       }
       block_argmax<L>(key, idx, tid, COOP_T);
       if (tid == 0) {
-        double *slot = cw.kslot + (size_t)q * COOP_KS;
 #pragma unroll
-        for (int l = 0; l < L; l++) slot[l] = key.x[l];
-        int *si = (int *)(slot + L);
-        si[0] = idx;
-        st_release(si + 1, (int)(j + 1));
+        for (int l = 0; l < L; l++) s_key[l] = key.x[l];
         s_cand = idx;
       }
       __syncthreads();
@@ -186,11 +182,12 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     //    candidate (SMSPs 0 and 1: Re p^2 and Im p^2 in parallel, the real
     //    reciprocal x of |p|^2 on warp 0, then Re p x and -Im p x in
     //    parallel; warps 4 and 5 keep off those two FP64 units meanwhile);
-    //    warps 2 and 6: the pending update of the candidate row and of row j,
+    //    warps 2 and 7: the pending update of the candidate row and of row j,
     //    published to their slots; once all four are done thread 0 releases
-    //    the flag.  Warp 3 does step 3 at the same time (it needs no FP64
-    //    unit until the swap).  The rest of the pending update goes in
-    //    32-element pieces to whole warps: 7 at once, the others when free.
+    //    the flag.  Warp 3 publishes the key and does step 3 at the same time
+    //    (it needs no FP64 unit until the swap).  The rest of the pending
+    //    update goes in 32-element pieces to whole warps: 6 at once, the
+    //    others when free.
     if ((w & 2) == 0) {
       __shared__ double s_inv[2 * L];  // Im p^2 accumulator, then x
       const bool act = has && lane == 0 && w < 2;
@@ -225,9 +222,9 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
 #pragma unroll
         for (int l = 0; l < L; l++) ws.part_rcp[(int64_t)q * 2 * L + w * L + l] = v.x[l];
       }
-    } else if (w == 2 || w == 6) {
+    } else if (w == 2 || w == 7) {
       // warp 2: the candidate row (and the row-j slot when it is row j);
-      // warp 6: row j when it is another row of this CTA
+      // warp 7: row j when it is another row of this CTA
       const int r = w == 2 ? cr : (jr != cr ? jr : -1);
       if (r >= 0) {
         double *dst = w == 2 ? cw.prow + (size_t)q * RW : cw.srow + (size_t)par * RW;
@@ -256,7 +253,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       }
       named_arrive(3, 96);  // rows cr and jr are final: warp 3 may swap them
     }
-    if (w == 0 || w == 1 || w == 2 || w == 6) {
+    if (w == 0 || w == 1 || w == 2 || w == 7) {
       named_sync(2, 128);
       if (has && tid == 0) {
         __threadfence();
@@ -264,6 +261,14 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       }
     }
     if (w == 3) {
+      if (lane == 0) {  // this CTA's best (key, row) to its slot, stamped
+        double *slot = cw.kslot + (size_t)q * COOP_KS;
+#pragma unroll
+        for (int l = 0; l < L; l++) slot[l] = s_key[l];
+        int *si = (int *)(slot + L);
+        si[0] = cand;
+        st_release(si + 1, (int)(j + 1));
+      }
       // 3. the winner over all key slots of this column: lane l takes slots
       //    l, l + 32, ...; their stamps are read together (relaxed) until
       //    all carry the column, then one fence orders the key reads after
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         for (int t = lane; t < RW; t += 32) su[t] = __ldcg(prow + t);
         if (lane < 2 * L) s_rcp[lane] = __ldcg(ws.part_rcp + (int64_t)part * 2 * L + lane);
       }
-      named_sync(3, 96);  // warps 2 and 6 are done with rows cr and jr
+      named_sync(3, 96);  // warps 2 and 7 are done with rows cr and jr
       if (ok && !zero) {
         if (own_p) {
           const double *srow = cw.srow + (size_t)par * RW;
