@@ -56,6 +56,10 @@ OZAKI_S = {"dd": 14, "td": 24, "qd": 32}
 # reported, scaled to the average trailing launch by n2^2, only while the
 # kernel source is the one it was taken on (sha1 of csrc/ozaki.cuh).
 OZ_TRAFFIC = {"dd": {"bytes": 971030272 + 477952256, "n2": 3968, "src_sha1": "cb83ea875dc66ff7beee53aa17073ebe7a24110c"}}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one cooperative panel
+# launch (the first 32-column sub-panel of n = 2048: m = 2048 rows), valid
+# while the kernel's source is unchanged
+PANEL_TRAFFIC = {"dd": {"bytes": 2218240 + 36608, "m": 2048, "w": 32, "src_sha1": "a8c5c09c55acb7e3f14cec7d491797c84913a32f"}}
 # unit roundoff exponents: u = 2^-104 / 2^-157 / 2^-209
 U_EXP = {"dd": 104, "td": 157, "qd": 209}
 
@@ -252,9 +256,19 @@ def panel_roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: di
             macs += rows * (ww - jc - 1) + rows  # rank-1 update + multiplier
     per_launch = macs * 4 * I_REAL[prec] / (panel_calls / steps)
     achieved = per_launch / (panel_ms / panel_calls * 1e-3)
+    traffic, note = None, None
+    cap = PANEL_TRAFFIC.get(prec)
+    if cap and method == "ozaki" and w == cap["w"]:
+        import hashlib
+        with open(os.path.join(ROOT, "paper_2403_16013_gb300", "csrc", "panel_coop.cuh"), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() == cap["src_sha1"]:
+                rows = [n - s0 for s0 in range(0, n, w)]
+                traffic = cap["bytes"] * (sum(rows) / len(rows)) / cap["m"]
+                note = "ncu dram read+write of one launch with m = 2048 rows, scaled to the average launch by rows"
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "T FP64-ops/s",
             "frac": achieved / FP64_OPS_PEAK, "peak_source": "nominal FP64 (1.25 TFLOP/s, FMA = 2)",
-            "traffic": None, "kernel": f"k_panel_coop<{LIMBS[prec]}> (latency bound: a serial FP64 chain per column)",
+            "traffic": traffic, "traffic_note": note,
+            "kernel": f"k_panel_coop<{LIMBS[prec]}> (latency bound: a serial FP64 chain per column)",
             "ops_per_launch": per_launch, "avg_launch_ms": panel_ms / panel_calls, "share_of_step": panel_ms / el_ms}
 
 
