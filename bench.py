@@ -367,8 +367,6 @@ def run_sweep(args):
     points = [("unblocked", 0)]
     for method in ("4m", "3m", "ozaki"):
         for nb in (16, 32, 64, 96, 128, 192, 256):
-            if method == "ozaki" and nb > 128:
-                continue
             points.append((method, nb))
     for method, nb in points:
         def step():

@@ -46,14 +46,14 @@ enum {
                              /*   Im = T3 - (T1 + T2)                                              */
   MCLU_METHOD_UNBLOCKED = 2, /* "Normal LU" of Sec. 3: right-looking row elimination, no GEMM    */
   MCLU_METHOD_OZAKI = 3      /* Ozaki-scheme update (Sec. 2.3): exact bf16 slice products on the */
-                             /*   tensor cores; block width nb <= 128 (default 128), factored as */
+                             /*   tensor cores; block width nb <= 256 (default 128), factored as */
                              /*   32-column sub-panels with Ozaki updates between them           */
 };
 
 /* Optional parameters of the *_ex factorisation calls (NULL = defaults). */
 typedef struct mclu_opts {
   int32_t nb;           /* panel width K of Sec. 3 (block size NDIM); 0 = 64 (128 for Ozaki); */
-                        /*   1..256 (1..128 for Ozaki)                                        */
+                        /*   1..256                                                           */
   int32_t method;       /* MCLU_METHOD_*; default MCLU_METHOD_4M                             */
   int32_t ozaki_slices; /* MCLU_METHOD_OZAKI: 0 or the precision's S (14 DD, 24 TD, 32 QD)      */
   int32_t reserved;     /* must be 0                                                          */

@@ -237,7 +237,6 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     if (method == MCLU_METHOD_OZAKI) {
       if (opts->ozaki_slices != 0 && opts->ozaki_slices != oz::Cfg<L>::S) return MCLU_ERR_UNSUPPORTED;
       if (opts->nb == 0) nb = 4 * oz::NB_MAX;  // 128: measured best at n = 4096 (64: -3%, 96: -1.3% DD)
-      if (nb > 4 * oz::NB_MAX) return -6;
     }
   }
   if (n > INT32_MAX - 1) return -1;
@@ -378,10 +377,11 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
           k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(W, jb);
           MCLU_LAUNCHED();
           constexpr int SB = oz::NB_MAX;  // 32: the sub-panel width
-          if (jb <= SB || L == 2) {
+          if (jb <= SB || (L == 2 && jb <= 128)) {
             // one CTA per column of W (the solve is FP64-latency bound, so
-            // the jb columns go to jb SMs); for DD this direct solve measured
-            // faster than the composition below (its FP64 chain is short)
+            // the jb columns go to jb SMs); for DD blocks up to 128 this
+            // direct solve measured faster than the composition below (its
+            // FP64 chain is short)
             int rc0 = launch_lsolve<L>(s, A, j0, (int)jb, W, jb, 0);
             if (rc0) return rc0;
           } else {

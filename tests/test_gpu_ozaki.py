@@ -128,6 +128,25 @@ def test_lu_ozaki_parity(api, orc, L, nb):
     assert diff <= 2.0 ** 10 * n * 2.0 ** -U_EXP[L] * np.abs(A[:, 0]).max() * max(1.0, np.abs(LUo[:, 0]).max())
 
 
+@pytest.mark.parametrize("L", [2, 3])
+def test_lu_ozaki_parity_wide_block(api, orc, L):
+    """Blocks of 256 columns (eight 32-column sub-panels), the last one
+    ragged (n = 300)."""
+    n = 300
+    A = inputs.gaussian_matrix(n, L, seed=5)
+    LU, ipiv, info = api.lu_factor(dev(A), method="ozaki", nb=256)
+    assert int(host(info)[0]) == 0
+    LUo, ipo, _, gap = orc.zgetrf(A)
+    ipg = host(ipiv)
+    mism = np.nonzero(ipg != ipo)[0]
+    if mism.size:
+        assert gap[mism[0]] < 2.0 ** -(53 * L - 16)
+    xr, xi = inputs.ones_x_true(n)
+    b = inputs.truncate_limbs(inputs.exact_rhs(A, xr, xi, L_out=4), L)
+    x = host(api.lu_solve(LU, ipiv, dev(b)))
+    assert backward_error(orc, A, x, b) <= bound(n, L)
+
+
 @pytest.mark.parametrize("L", [2, 4])
 @pytest.mark.parametrize("nb", [16, 64])
 def test_lu_ozaki_known_factor_bit_exact(api, L, nb):
