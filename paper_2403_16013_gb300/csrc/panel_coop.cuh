@@ -361,8 +361,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
           if (zero && *ws.info == 0) *ws.info = (int)(j + 1);
         }
       }
-    }
-    if (pend) {  // warp 3 joins once step 3 is done
+    } else if (pend) {
       const int rlo = (int)max((int64_t)0, j - rbeg);  // rows i > j - 1
       const int nrow = nr - rlo, ncol = nb - jc - 1;
       const int tot = nrow > 0 ? nrow * ncol : 0;
