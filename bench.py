@@ -268,7 +268,8 @@ def panel_roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: di
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "T FP64-ops/s",
             "frac": achieved / FP64_OPS_PEAK, "peak_source": "nominal FP64 (1.25 TFLOP/s, FMA = 2)",
             "traffic": traffic, "traffic_note": note,
-            "kernel": f"k_panel_coop<{LIMBS[prec]}> (latency bound: a serial FP64 chain per column)",
+            "kernel": f"{'k_panel_coop' if LIMBS[prec] == 2 else 'k_panel_team'}<{LIMBS[prec]}> "
+                      "(latency bound: a serial FP64 chain per column)",
             "ops_per_launch": per_launch, "avg_launch_ms": panel_ms / panel_calls, "share_of_step": panel_ms / el_ms}
 
 

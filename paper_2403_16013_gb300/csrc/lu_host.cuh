@@ -13,6 +13,7 @@
 #include "lu_kernels.cuh"
 #include "ozaki.cuh"
 #include "panel_coop.cuh"
+#include "panel_team.cuh"
 
 namespace mclu {
 
@@ -154,9 +155,10 @@ int launch_lsolve(cudaStream_t s, View A, int64_t k0, int bs, View X, int64_t nc
                                                 xrow0);
 }
 
-// Cooperative panel factorisation.  Returns 0 (launched), 1 (the grid or its
-// shared memory does not fit: caller falls back to per-column launches) or a
-// CUDA error code.
+// Cooperative panel factorisation (k_panel_coop for DD, k_panel_team for TD
+// and QD: measured faster for each).  Returns 0 (launched), 1 (the grid or
+// its shared memory does not fit: caller falls back to per-column launches)
+// or a CUDA error code.
 template <int L>
 int launch_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int32_t *ipiv, PanelWS<L> ws, CoopWS cw,
                       cudaStream_t s) {
@@ -171,17 +173,18 @@ int launch_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int32_t *ipiv
   // owned rows + the pivot rows of two columns + the multipliers' partial products
   const size_t smem = (((size_t)rpc + 2) * nb * 2 * L + (size_t)4 * rpc * L) * sizeof(double);
   if (smem > 200 * 1024) return 1;
+  auto kern = L == 2 ? k_panel_coop<L> : k_panel_team<L>;
   if (per_sm < 0) {
-    MCLU_TRY(cudaFuncSetAttribute(k_panel_coop<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    MCLU_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     per_sm = 0;
   }
   int occ = 0;
-  MCLU_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_panel_coop<L>, COOP_T, smem));
+  MCLU_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, COOP_T, smem));
   if ((int64_t)occ * sms < G) return 1;
   int64_t a_n = n, a_j0 = j0, a_jend = jend;
   int a_rpc = rpc;
   void *args[] = {&A, &a_n, &a_j0, &a_jend, &a_rpc, &ipiv, &ws, &cw};
-  MCLU_TRY(cudaLaunchCooperativeKernel((const void *)k_panel_coop<L>, dim3(G), dim3(COOP_T), args, smem, s));
+  MCLU_TRY(cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(COOP_T), args, smem, s));
   note_launch();
   return 0;
 }
