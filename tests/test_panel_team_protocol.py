@@ -1,0 +1,132 @@
+"""Deadlock check of k_panel_team's named-barrier protocol (host model, no GPU).
+
+The kernel's warps are modelled as threads that execute, per panel column,
+the same sequence of named-barrier operations as csrc/panel_team.cuh:
+producers `bar.arrive`, consumers `bar.sync`, a phase completing when the
+barrier's thread count has arrived.  Every path is covered: ordinary columns,
+zero pivots (no elimination), and a timed-out exchange at the first, a middle
+and the last column (the factor team releases the update team at its next go
+signal).  A wait that does not complete within two seconds is a deadlock.
+"""
+import threading
+
+import pytest
+
+COUNTS = {"MAIN": 128, "RCP": 64, "DONE": 224, "PUB": 96, "SWAP": 128, "GO": 256, "ALL": 256}
+
+
+class NamedBarrier:
+    def __init__(self, count):
+        self.count, self.arrived, self.gen = count, 0, 0
+        self.cv = threading.Condition()
+
+    def _arrive(self, n):
+        self.arrived += n
+        if self.arrived > self.count:
+            raise RuntimeError("more arrivals than the barrier's count")
+        if self.arrived == self.count:
+            self.arrived = 0
+            self.gen += 1
+            self.cv.notify_all()
+            return True
+        return False
+
+    def sync(self, n=32):
+        with self.cv:
+            g = self.gen
+            if self._arrive(n):
+                return
+            if not self.cv.wait_for(lambda: self.gen != g, timeout=2.0):
+                raise RuntimeError("deadlock")
+
+    def arrive(self, n=32):
+        with self.cv:
+            self._arrive(n)
+
+
+def run_protocol(nb, zero_cols, err_col):
+    B = {k: NamedBarrier(v) for k, v in COUNTS.items()}
+    sh = {"ok": 1, "zero": 0}
+    errors, lock = [], threading.Lock()
+
+    def update_warp(w):
+        for jc in range(nb):
+            B["GO"].sync()
+            if not sh["ok"]:
+                break
+            B["DONE"].arrive()
+        B["ALL"].sync()
+
+    def factor_warp(w):
+        B["GO"].arrive()
+        for jc in range(nb):
+            B["MAIN"].sync()  # keys: warp results
+            B["MAIN"].sync()  # keys: CTA result
+            if w < 3:
+                if w < 2:
+                    B["RCP"].sync()
+                    B["RCP"].sync()
+                B["DONE"].sync()
+                B["PUB"].sync()
+                B["SWAP"].arrive()
+            else:
+                B["SWAP"].sync()
+                with lock:
+                    if jc == err_col:
+                        sh["ok"] = 0
+                    sh["zero"] = 1 if jc in zero_cols else 0
+            B["MAIN"].sync()
+            if not sh["ok"]:
+                if jc + 1 < nb:
+                    B["GO"].arrive()
+                break
+            if sh["zero"]:
+                if jc + 1 < nb:
+                    B["MAIN"].sync()
+                    B["GO"].arrive()
+                continue
+            B["MAIN"].sync()  # multiplier products
+            if jc + 1 < nb:
+                B["MAIN"].sync()  # multipliers final
+                B["GO"].arrive()
+                B["MAIN"].sync()  # next column's products
+            B["MAIN"].sync()  # end of the column
+        B["ALL"].sync()
+
+    def wrap(f, w):
+        try:
+            f(w)
+        except Exception as e:  # noqa: BLE001
+            errors.append((w, repr(e)))
+
+    ts = [threading.Thread(target=wrap, args=(factor_warp if w < 4 else update_warp, w)) for w in range(8)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return errors
+
+
+@pytest.mark.parametrize("nb", [1, 2, 3, 5, 32])
+def test_panel_team_protocol_deadlock_free(nb):
+    cases = [((), -1), ((0,), -1), ((nb - 1,), -1), (tuple(range(nb)), -1),
+             ((), 0), ((), nb - 1), ((1,), nb // 2)]
+    for zero_cols, err_col in cases:
+        assert run_protocol(nb, set(zero_cols), err_col) == [], (nb, zero_cols, err_col)
+
+
+def test_protocol_model_detects_a_missing_arrival():
+    """The model itself: dropping the factor team's first go signal deadlocks."""
+    B = NamedBarrier(64)
+    out = []
+
+    def waiter():
+        try:
+            B.sync()
+        except RuntimeError as e:
+            out.append(str(e))
+
+    t = threading.Thread(target=waiter)
+    t.start()
+    t.join()
+    assert out == ["deadlock"]
