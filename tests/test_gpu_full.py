@@ -1,5 +1,5 @@
 """Full-size checks at n = 4096 in the benchmark's launch configuration
-(blocked, nb = 64 with the 4M and 3M updates, nb = 32 with the Ozaki update), by properties that hold at any
+(blocked, nb = 64 with the 4M and 3M updates, nb = 128 with the Ozaki update), by properties that hold at any
 size and that the oracle can evaluate one output at a time:
 
 * backward error with the exact residual: ||b - A x|| / (||A|| ||x||) <= 16 n u;
@@ -35,12 +35,14 @@ def _apply_pivots(A, ipiv):
     return P
 
 
-@pytest.mark.parametrize("prec,method", [("dd", "4m"), ("dd", "3m"), ("td", "4m"), ("qd", "4m"),
-                                         ("dd", "ozaki"), ("td", "ozaki"), ("qd", "ozaki")])
-def test_full_size(api, orc, prec, method):
+@pytest.mark.parametrize("prec,method,n", [("dd", "4m", 4096), ("dd", "3m", 4096), ("td", "4m", 4096),
+                                           ("qd", "4m", 4096), ("dd", "ozaki", 4096), ("td", "ozaki", 4096),
+                                           ("qd", "ozaki", 4096),
+                                           # more than 32 panel rows per CTA (152 CTAs) in the first panels
+                                           ("dd", "ozaki", 5120), ("td", "ozaki", 5120)])
+def test_full_size(api, orc, prec, method, n):
     import torch
     L = {"dd": 2, "td": 3, "qd": 4}[prec]
-    n = 4096
     A = inputs.gaussian_matrix(n, L, seed=1)
     b = inputs.complex_gaussian_vector(n, L, seed=2)
     Ad = dev(A)
