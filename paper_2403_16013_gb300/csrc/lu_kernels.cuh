@@ -230,22 +230,6 @@ __device__ int write_partial(R<L> key, int idx, const Z<L> &rcp, PanelWS<L> ws, 
   return w;
 }
 
-// Block argmax of (key, row) published as the block's partial q (key and
-// row only); returns the winning row to every thread.
-template <int L>
-__device__ int write_partial_key(R<L> key, int idx, PanelWS<L> ws, int q, int tid, int nthr) {
-  block_argmax<L>(key, idx, tid, nthr);
-  __shared__ int s_w;
-  if (tid == 0) {
-#pragma unroll
-    for (int l = 0; l < L; l++) ws.part_key[(int64_t)q * L + l] = key.x[l];
-    ws.part_idx[q] = idx;
-    s_w = idx;
-  }
-  __syncthreads();
-  return s_w;
-}
-
 // True in exactly one CTA per launch: the last one to arrive.
 __device__ __forceinline__ bool arrive_last(int *counter, int nblocks, int tid) {
   __shared__ int s_last;
