@@ -147,6 +147,28 @@ def test_lu_ozaki_parity_wide_block(api, orc, L):
     assert backward_error(orc, A, x, b) <= bound(n, L)
 
 
+@pytest.mark.parametrize("L", [2, 3])
+@pytest.mark.parametrize("zc", [0, 7, 31, 32, 63, 71])
+def test_lu_ozaki_zero_column(api, orc, L, zc):
+    """A zero column stays zero through the elimination: its step has no
+    pivot (info = zc + 1, no swap, no multipliers) and the factorisation goes
+    on.  Columns at the start, inside and at the end of a 32-column
+    sub-panel, and the last column (one block of 72: DD runs k_panel_coop,
+    TD k_panel_team)."""
+    n = 72
+    A = inputs.gaussian_matrix(n, L, seed=4)
+    A[:, :, zc, :] = 0.0
+    LU, ipiv, info = api.lu_factor(dev(A), method="ozaki")
+    LUo, ipo, info_o, gap = orc.zgetrf(A)
+    assert int(host(info)[0]) == info_o == zc + 1
+    ipg = host(ipiv)
+    mism = np.nonzero(ipg != ipo)[0]
+    if mism.size:
+        assert gap[mism[0]] < 2.0 ** -(53 * L - 16)
+    diff = np.abs((host(LU) - LUo).sum(axis=1)).max()
+    assert diff <= 2.0 ** 10 * n * 2.0 ** -U_EXP[L] * np.abs(A[:, 0]).max() * max(1.0, np.abs(LUo[:, 0]).max())
+
+
 @pytest.mark.parametrize("L", [2, 4])
 @pytest.mark.parametrize("nb", [16, 64])
 def test_lu_ozaki_known_factor_bit_exact(api, L, nb):
