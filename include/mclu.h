@@ -218,6 +218,19 @@ const char *mclu_status_string(int status);
 /* Library version as "major.minor.patch". */
 const char *mclu_version(void);
 
+/*
+ * mclu_selftest_wait_timeout: runs, on the current device, the bounded wait
+ * that the cooperative panel kernels use between CTAs (a clock64 budget of
+ * about one second) on a device flag that nothing sets, and writes to
+ * *status (host) the status word the kernel left: 1 when the wait ran out
+ * and the kernel recorded it and returned (what the panels then report
+ * through info < 0), 0 otherwise.  Nothing faults or hangs; the context
+ * stays usable.  Allocates and frees 8 bytes of device memory and
+ * synchronises the device.  Returns 0, -1 for a NULL status, or a CUDA
+ * error code.
+ */
+int mclu_selftest_wait_timeout(int32_t *status);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,7 @@ def _declare(lib):
     lib.zgetrf_dd_noalloc_max_n.argtypes, lib.zgetrf_dd_noalloc_max_n.restype = [], i64
     lib.mclu_status_string.argtypes, lib.mclu_status_string.restype = [ci], C.c_char_p
     lib.mclu_version.argtypes, lib.mclu_version.restype = [], C.c_char_p
+    lib.mclu_selftest_wait_timeout.argtypes, lib.mclu_selftest_wait_timeout.restype = [C.POINTER(C.c_int32)], ci
     lib.mclu_launch_count.argtypes, lib.mclu_launch_count.restype = [], C.c_uint64
     lib.mclu_profile_begin.argtypes, lib.mclu_profile_begin.restype = [C.c_uint32], ci
     lib.mclu_profile_end.argtypes, lib.mclu_profile_end.restype = [C.POINTER(C.c_double),
@@ -85,6 +86,14 @@ def profile_end() -> dict:
     cnt = (C.c_int64 * n)()
     check(load().mclu_profile_end(ms, cnt, n), "mclu_profile_end")
     return {k: (ms[i], cnt[i]) for i, k in enumerate(PROFILE_KINDS)}
+
+
+def selftest_wait_timeout() -> int:
+    """mclu_selftest_wait_timeout: the status word left by the panels'
+    bounded inter-CTA wait on a flag that nothing sets (1 = ran out)."""
+    st = C.c_int32(-1)
+    check(load().mclu_selftest_wait_timeout(C.byref(st)), "mclu_selftest_wait_timeout")
+    return int(st.value)
 
 
 def status_string(rc: int) -> str:

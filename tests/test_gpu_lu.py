@@ -116,3 +116,17 @@ def test_multiple_rhs_and_padding(api, orc):
     assert np.array_equal(host(ipiv), ipo)
     Xo = orc.zgetrs(LUo, ipo, Bm)
     assert np.abs((X - Xo).sum(axis=1)).max() <= 2.0 ** 12 * n * 2.0 ** -U_EXP[L] * np.abs(Xo[:, 0]).max()
+
+
+def test_bounded_wait_runs_out_and_context_survives(api, orc):
+    """The panels' inter-CTA wait on a flag that nothing sets runs out within
+    its budget and records it in the status word; the context stays usable
+    (a factorisation right after it matches the oracle)."""
+    from paper_2403_16013_gb300 import binding
+    assert binding.selftest_wait_timeout() == 1
+    n, L = 40, 2
+    A = inputs.gaussian_matrix(n, L, seed=8)
+    LU, ipiv, info = api.lu_factor(dev(A), method="ozaki")
+    LUo, ipo, info_o, _ = orc.zgetrf(A)
+    assert int(host(info)[0]) == info_o == 0
+    assert np.array_equal(host(ipiv), ipo)
