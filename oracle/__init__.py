@@ -45,6 +45,8 @@ def lib():
             "orc_normalize_rows": (None, [i64, ci, _D, _I32]),
             "orc_zgetrf": (ci, [ci, i64, _D, i64, _I32, _I32, _D]),
             "orc_zgetrs": (ci, [ci, C.c_char, i64, i64, _D, i64, _I32, _D, i64]),
+            "orc_dgetrf": (ci, [ci, i64, _D, i64, _I32, _I32, _D]),
+            "orc_dgetrs": (ci, [ci, C.c_char, i64, i64, _D, i64, _I32, _D, i64]),
             "orc_zgemm": (ci, [ci, ci, ci, i64, i64, i64, _D, i64, _D, i64, _D, i64]),
             "orc_exact_residual": (ci, [ci, ci, ci, ci, i64, i64, _D, i64, _D, i64, _D, i64, _D]),
             "orc_exact_entries": (ci, [ci, ci, ci, i64, i64, i64, _D, i64, _D, i64, _D, i64, ci, ci, i64,
@@ -153,6 +155,29 @@ def zgetrs(LU: np.ndarray, ipiv: np.ndarray, B: np.ndarray, trans: str = "N") ->
     _, _, nrhs, ldb = X.shape
     ip = np.ascontiguousarray(ipiv, np.int32)
     _check(lib().orc_zgetrs(L, trans.encode(), n, nrhs, _p(LU), lda, _p(ip), _p(X), ldb), "zgetrs")
+    return X
+
+
+def dgetrf(A: np.ndarray):
+    """Real unblocked GEPP (one plane per limb).  A: [L, n, lda] (copied).
+    Returns (LU, ipiv, info, gap)."""
+    LU = np.ascontiguousarray(A, np.float64).copy()
+    L, n, lda = LU.shape
+    ipiv = np.zeros(max(n, 1), np.int32)
+    info = np.zeros(1, np.int32)
+    gap = np.zeros(max(n, 1), np.float64)
+    _check(lib().orc_dgetrf(L, n, _p(LU), lda, _p(ipiv), _p(info), _p(gap)), "dgetrf")
+    return LU, ipiv[:n], int(info[0]), gap[:n]
+
+
+def dgetrs(LU: np.ndarray, ipiv: np.ndarray, B: np.ndarray, trans: str = "N") -> np.ndarray:
+    """Real solve with the factors of dgetrf.  B: [L, nrhs, ldb] (copied); trans 'N' or 'T'."""
+    LU = np.ascontiguousarray(LU, np.float64)
+    X = np.ascontiguousarray(B, np.float64).copy()
+    L, n, lda = LU.shape
+    _, nrhs, ldb = X.shape
+    ip = np.ascontiguousarray(ipiv, np.int32)
+    _check(lib().orc_dgetrs(L, trans.encode(), n, nrhs, _p(LU), lda, _p(ip), _p(X), ldb), "dgetrs")
     return X
 
 

@@ -950,3 +950,199 @@ int orc_make_ill_conditioned(int L, int64_t n, int h, const double *V1, const do
   for (int j = h - 1; j >= 0; j--) apply_reflector(L, n, A, V1 + (size_t)j * 2 * n, 1);
   return g_err ? 1 : 0;
 }
+
+/* ------------------------------------------------ real LU and solve -- */
+
+/*
+ * The real multi-component LU that the complex one builds on (the author's
+ * earlier real DD/TD/QD LU, Sec. 1; the same blocked/"Normal" structure,
+ * Sec. 3), one plane per limb: limb plane l of a real L-limb matrix starts at
+ * A + l*ld*ncols, element (i, j) at offset j*ld + i.  Pivot = argmax of the
+ * exact |a_ik| over i >= k, ties to the lowest row; the column is scaled by
+ * the MC reciprocal 1/a_kk (long division of 1 by the pivot, the "inv" of
+ * Sec. 2.2); a_ij -= l_ik u_kj with the MC product and difference; info =
+ * first exactly-zero pivot; gap as in orc_zgetrf.
+ */
+static inline size_t rofs(int l, int64_t ld, int64_t ncols) { return (size_t)l * (size_t)ld * (size_t)ncols; }
+
+static void ld_rel(int L, const double *A, int64_t ld, int64_t ncols, int64_t i, int64_t j, double *z) {
+  size_t o = (size_t)j * ld + i;
+  for (int l = 0; l < L; l++) z[l] = A[rofs(l, ld, ncols) + o];
+}
+
+static void st_rel(int L, double *A, int64_t ld, int64_t ncols, int64_t i, int64_t j, const double *z) {
+  size_t o = (size_t)j * ld + i;
+  for (int l = 0; l < L; l++) A[rofs(l, ld, ncols) + o] = z[l];
+}
+
+static void swap_rows_real(int L, double *A, int64_t ld, int64_t ncols, int64_t r1, int64_t r2) {
+  if (r1 == r2) return;
+  for (int l = 0; l < L; l++) {
+    double *P = A + rofs(l, ld, ncols);
+    for (int64_t j = 0; j < ncols; j++) {
+      double t = P[j * ld + r1];
+      P[j * ld + r1] = P[j * ld + r2];
+      P[j * ld + r2] = t;
+    }
+  }
+}
+
+/* Exact |a| as a normalised expansion (for pivot comparisons). */
+static int abs_exact(int L, const double *a, double *t) {
+  int s = mc_sign(L, a);
+  for (int i = 0; i < L; i++) t[i] = s < 0 ? -a[i] : a[i];
+  return normalize(t, L);
+}
+
+int orc_dgetrf(int L, int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, double *gap) {
+  if (L < 2 || L > MAXL) return -1;
+  if (n < 0) return -2;
+  if (lda < (n > 1 ? n : 1)) return -4;
+  *info = 0;
+  double *keys = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * MAXL);
+  int *klen = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  if (!keys || !klen) { free(keys); free(klen); return -100; }
+  const double one[MAXL] = {1.0, 0.0, 0.0, 0.0};
+  for (int64_t k = 0; k < n; k++) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = k; i < n; i++) {
+      double z[MAXL];
+      ld_rel(L, A, lda, n, i, k, z);
+      klen[i] = abs_exact(L, z, keys + (size_t)i * MAXL);
+    }
+    int64_t p = k;
+    for (int64_t i = k + 1; i < n; i++)
+      if (exp_cmp(keys + (size_t)i * MAXL, klen[i], keys + (size_t)p * MAXL, klen[p]) > 0) p = i;
+    if (gap) {
+      double k1 = klen[p] ? keys[(size_t)p * MAXL] : 0.0, k2 = 0.0;
+      int have2 = 0;
+      for (int64_t i = k; i < n; i++) {
+        if (i == p) continue;
+        double v = klen[i] ? keys[(size_t)i * MAXL] : 0.0;
+        if (!have2 || v > k2) k2 = v;
+        have2 = 1;
+      }
+      gap[k] = (have2 && k1 > 0.0) ? (k1 - k2) / k1 : 1.0;
+    }
+    ipiv[k] = (int32_t)(p + 1);
+    if (klen[p] == 0) {
+      if (*info == 0) *info = (int32_t)(k + 1);
+      continue;
+    }
+    swap_rows_real(L, A, lda, n, k, p);
+    double piv[MAXL], r[MAXL];
+    ld_rel(L, A, lda, n, k, k, piv);
+    mc_div(L, one, piv, r);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = k + 1; i < n; i++) {
+      double a[MAXL], l[MAXL];
+      ld_rel(L, A, lda, n, i, k, a);
+      mc_mul(L, a, r, l);
+      st_rel(L, A, lda, n, i, k, l);
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = k + 1; j < n; j++) {
+      double u[MAXL];
+      ld_rel(L, A, lda, n, k, j, u);
+      for (int64_t i = k + 1; i < n; i++) {
+        double l[MAXL], a[MAXL], t[MAXL], z[MAXL];
+        ld_rel(L, A, lda, n, i, k, l);
+        ld_rel(L, A, lda, n, i, j, a);
+        mc_mul(L, l, u, t);
+        mc_sub(L, a, t, z);
+        st_rel(L, A, lda, n, i, j, z);
+      }
+    }
+  }
+  free(keys);
+  free(klen);
+  return g_err ? 1 : 0;
+}
+
+/*
+ * Solve with the factors of orc_dgetrf.  trans 'N': A X = B; 'T': A^T X = B
+ * (U^T, then L^T, then P^T).  B: n x nrhs limb planes (plane stride
+ * ldb*nrhs), overwritten by X.
+ */
+int orc_dgetrs(int L, char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda, const int32_t *ipiv,
+               double *B, int64_t ldb) {
+  if (L < 2 || L > MAXL) return -1;
+  if (trans != 'N' && trans != 'T') return -2;
+  if (n < 0) return -3;
+  if (nrhs < 0) return -4;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t c = 0; c < nrhs; c++) {
+    double x[MAXL], y[MAXL], a[MAXL], t[MAXL];
+    if (trans == 'N') {
+      for (int64_t k = 0; k < n; k++) {
+        int64_t p = ipiv[k] - 1;
+        if (p != k) {
+          ld_rel(L, B, ldb, nrhs, k, c, x);
+          ld_rel(L, B, ldb, nrhs, p, c, y);
+          st_rel(L, B, ldb, nrhs, k, c, y);
+          st_rel(L, B, ldb, nrhs, p, c, x);
+        }
+      }
+      for (int64_t k = 0; k < n; k++) { /* unit lower */
+        ld_rel(L, B, ldb, nrhs, k, c, x);
+        for (int64_t i = k + 1; i < n; i++) {
+          ld_rel(L, A, lda, n, i, k, a);
+          ld_rel(L, B, ldb, nrhs, i, c, y);
+          mc_mul(L, a, x, t);
+          mc_sub(L, y, t, y);
+          st_rel(L, B, ldb, nrhs, i, c, y);
+        }
+      }
+      for (int64_t k = n - 1; k >= 0; k--) { /* upper */
+        ld_rel(L, B, ldb, nrhs, k, c, x);
+        ld_rel(L, A, lda, n, k, k, a);
+        mc_div(L, x, a, x);
+        st_rel(L, B, ldb, nrhs, k, c, x);
+        for (int64_t i = 0; i < k; i++) {
+          ld_rel(L, A, lda, n, i, k, a);
+          ld_rel(L, B, ldb, nrhs, i, c, y);
+          mc_mul(L, a, x, t);
+          mc_sub(L, y, t, y);
+          st_rel(L, B, ldb, nrhs, i, c, y);
+        }
+      }
+    } else {
+      /* U^T w = b: lower triangular, (U^T)[i, k] = U[k, i] */
+      for (int64_t k = 0; k < n; k++) {
+        ld_rel(L, B, ldb, nrhs, k, c, x);
+        ld_rel(L, A, lda, n, k, k, a);
+        mc_div(L, x, a, x);
+        st_rel(L, B, ldb, nrhs, k, c, x);
+        for (int64_t i = k + 1; i < n; i++) {
+          ld_rel(L, A, lda, n, k, i, a);
+          ld_rel(L, B, ldb, nrhs, i, c, y);
+          mc_mul(L, a, x, t);
+          mc_sub(L, y, t, y);
+          st_rel(L, B, ldb, nrhs, i, c, y);
+        }
+      }
+      /* L^T z = w: unit upper, (L^T)[i, k] = L[k, i] */
+      for (int64_t k = n - 1; k >= 0; k--) {
+        ld_rel(L, B, ldb, nrhs, k, c, x);
+        for (int64_t i = 0; i < k; i++) {
+          ld_rel(L, A, lda, n, k, i, a);
+          ld_rel(L, B, ldb, nrhs, i, c, y);
+          mc_mul(L, a, x, t);
+          mc_sub(L, y, t, y);
+          st_rel(L, B, ldb, nrhs, i, c, y);
+        }
+      }
+      /* x = P^T z: undo the swaps in reverse order */
+      for (int64_t k = n - 1; k >= 0; k--) {
+        int64_t p = ipiv[k] - 1;
+        if (p != k) {
+          ld_rel(L, B, ldb, nrhs, k, c, x);
+          ld_rel(L, B, ldb, nrhs, p, c, y);
+          st_rel(L, B, ldb, nrhs, k, c, y);
+          st_rel(L, B, ldb, nrhs, p, c, x);
+        }
+      }
+    }
+  }
+  return g_err ? 1 : 0;
+}

@@ -65,3 +65,42 @@ def known_factor_case(n: int, L: int, seed: int):
     xr = rng.integers(-8, 9, n)
     xi = rng.integers(-8, 9, n)
     return A, np.array(ipiv, np.int32), packed, xr, xi
+
+
+def known_factor_case_real(n: int, L: int, seed: int):
+    """The real counterpart of ``known_factor_case``: A = P^T L U exactly with
+    L unit lower, real dyadic multipliers |l_ij| <= 1/2, U upper with dyadic
+    entries and diagonal entries +-2^t (1/u_kk dyadic).  Exact partial pivoting
+    on |a| picks at step k the unique candidate whose multiplier is 1.
+    Returns A [L, n, n], ipiv, the packed factors [L, n, n] and a dyadic
+    integer x."""
+    rng = np.random.default_rng(seed)
+    Lm = [[Fraction(0)] * n for _ in range(n)]
+    Um = [[Fraction(0)] * n for _ in range(n)]
+    for i in range(n):
+        Lm[i][i] = Fraction(1)
+        for j in range(i):
+            Lm[i][j] = Fraction(int(rng.integers(-4, 5)), 8)        # |l| <= 1/2
+        t = int(rng.integers(-2, 3))
+        Um[i][i] = Fraction(int(rng.choice([-1, 1]))) * Fraction(2) ** t
+        for j in range(i + 1, n):
+            Um[i][j] = Fraction(int(rng.integers(-16, 17)), 4)
+    sigma = rng.permutation(n)                   # row t of L U goes to row sigma[t] of A
+    A = np.zeros((L, n, n))
+    for t in range(n):
+        for j in range(n):
+            v = sum((Lm[t][k] * Um[k][j] for k in range(min(t, j) + 1)), Fraction(0))
+            assert float(v) == v
+            A[0, j, sigma[t]] = float(v)
+    cur = list(range(n))
+    ipiv = []
+    for k in range(n):
+        p = cur.index(int(sigma[k]), k)
+        ipiv.append(p + 1)
+        cur[k], cur[p] = cur[p], cur[k]
+    packed = np.zeros((L, n, n))
+    for i in range(n):
+        for j in range(n):
+            packed[0, j, i] = float(Lm[i][j] if i > j else Um[i][j])
+    x = rng.integers(-8, 9, n)
+    return A, np.array(ipiv, np.int32), packed, x
