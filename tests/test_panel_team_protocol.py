@@ -1,7 +1,9 @@
-"""Deadlock check of k_panel_team's named-barrier protocol (host model, no GPU).
+"""Deadlock check of the cooperative panels' named-barrier protocols (host
+model, no GPU): k_panel_team (TD, QD) and k_panel_coop (DD).
 
 The kernel's warps are modelled as threads that execute, per panel column,
-the same sequence of named-barrier operations as csrc/panel_team.cuh:
+the same sequence of barrier operations as csrc/panel_team.cuh and
+csrc/panel_coop.cuh:
 producers `bar.arrive`, consumers `bar.sync`, a phase completing when the
 barrier's thread count has arrived.  Every path is covered: ordinary columns,
 zero pivots (no elimination), and a timed-out exchange at the first, a middle
@@ -130,3 +132,62 @@ def test_protocol_model_detects_a_missing_arrival():
     t.start()
     t.join()
     assert out == ["deadlock"]
+
+
+def run_coop_protocol(nb, zero_cols, err_col):
+    """k_panel_coop: __syncthreads (all 8 warps), bar 1 (warps 0, 1, 4, 5:
+    the reciprocal), bar 2 (warps 0, 1, 2, 7: release of the flag), bar 3
+    (warps 2 and 7 arrive, warp 3 waits before its swap)."""
+    B = {"ALL": NamedBarrier(256), "B1": NamedBarrier(128), "B2": NamedBarrier(128), "B3": NamedBarrier(96)}
+    sh = {"ok": 1, "zero": 0}
+    errors, lock = [], threading.Lock()
+
+    def warp(w):
+        B["ALL"].sync()                       # rows loaded
+        for jc in range(nb):
+            B["ALL"].sync(); B["ALL"].sync()  # keys: block argmax
+            B["ALL"].sync()                   # keys: the CTA's candidate
+            if w in (0, 1, 4, 5):
+                B["B1"].sync(); B["B1"].sync()
+            elif w in (2, 7):
+                B["B3"].arrive()
+            if w in (0, 1, 2, 7):
+                B["B2"].sync()
+            if w == 3:
+                B["B3"].sync()
+                with lock:
+                    if jc == err_col:
+                        sh["ok"] = 0
+                    sh["zero"] = 1 if jc in zero_cols else 0
+            B["ALL"].sync()                   # update and exchange done
+            if not sh["ok"]:
+                return
+            if sh["zero"]:
+                B["ALL"].sync()
+                continue
+            B["ALL"].sync()                   # multiplier products
+            B["ALL"].sync()                   # multipliers
+            if jc + 1 < nb:
+                B["ALL"].sync()               # next column's products
+            B["ALL"].sync()                   # end of the column
+
+    def wrap(w):
+        try:
+            warp(w)
+        except Exception as e:  # noqa: BLE001
+            errors.append((w, repr(e)))
+
+    ts = [threading.Thread(target=wrap, args=(w,)) for w in range(8)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return errors
+
+
+@pytest.mark.parametrize("nb", [1, 2, 3, 5, 32])
+def test_panel_coop_protocol_deadlock_free(nb):
+    cases = [((), -1), ((0,), -1), ((nb - 1,), -1), (tuple(range(nb)), -1),
+             ((), 0), ((), nb - 1), ((1,), nb // 2)]
+    for zero_cols, err_col in cases:
+        assert run_coop_protocol(nb, set(zero_cols), err_col) == [], (nb, zero_cols, err_col)
