@@ -13,10 +13,11 @@
 //   * the update team (warps 5-7; warp 4 only keeps the barrier counts)
 //     applies column j-1's rank-1 update to the columns after j from the
 //     moment column j-1's multipliers are final until the factor team needs
-//     the rows for column j: it overlaps the next column's update, keys,
-//     reciprocal and exchange instead of only the exchange.
+//     the rows for column j: it overlaps the factor team's update of the
+//     next pivot column, its keys, reciprocal and exchange instead of only
+//     the exchange.
 // With TD and QD the long reciprocal chain leaves room for the whole update
-// (measured at n = 4096: panel TD 128.3 -> 123.7 ms, QD 282.3 -> 266.6 ms);
+// (measured at n = 4096: panel TD 128.3 -> 123.1 ms, QD 282.3 -> 266.1 ms);
 // with DD the shorter chain does not, and k_panel_coop stays faster.
 // Every global wait is bounded (clock64 budget); a timeout sets *status, the
 // factor team releases the update team at its next go signal and the CTA
