@@ -104,7 +104,9 @@ int zgetrf_qd_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info
  *   A, lda, ipiv, info, stream  as in zgetrf_dd_ex (info may be NULL)
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it: make that first call before any stream
- * capture.  All calls share the array: calls that can overlap on the GPU
+ * capture.  The cache is never refreshed: after a cudaDeviceReset of a
+ * device, the cached address is stale, so a process that resets a device must
+ * not call this entry point on that device again.  All calls share the array: calls that can overlap on the GPU
  * (several streams or host threads) race and must be serialised by the
  * caller.  Counters that must start at zero are cleared by every call.
  */

@@ -14,7 +14,10 @@
 // exits.  Host code cannot use the array's name as a device address, so the
 // first call on each device looks the address up with cudaGetSymbolAddress
 // (with that device current) and caches it; that first call should happen
-// before any stream capture starts.  Every call shares the one array: calls
+// before any stream capture starts.  The cache is not refreshed after a
+// cudaDeviceReset (which unloads the module and may place the array
+// elsewhere): a process that resets a device must not call this entry point on
+// that device again.  Every call shares the one array: calls
 // that may overlap on the GPU (different streams, or several host threads)
 // race on it and must be serialised by the caller.  The counters and flags
 // that must start at zero are cleared at the start of every call.

@@ -920,6 +920,15 @@ template <int L>
 int gemm(bool beta, View A, View B, View C, int64_t m, int64_t n, int64_t k, void *ws, int *status, cudaStream_t s,
          void (*note)()) {
   if (m <= 0 || n <= 0) return 0;
+  if (k == 0) {  // nothing to multiply (and nothing to split): C unchanged (beta) or zero
+    if (!beta) {
+      for (int pl = 0; pl < 2 * L; pl++) {
+        cudaError_t e = cudaMemset2DAsync(C.p + (int64_t)pl * C.ps, C.ld * sizeof(double), 0, m * sizeof(double), n, s);
+        if (e != cudaSuccess) return (int)e;
+      }
+    }
+    return 0;
+  }
   const Sizes<L> z = sizes<L>(m, n, k);
   int rc = split<L>(A, B, m, n, k, ws, s, note);
   if (rc) return rc;
@@ -938,15 +947,6 @@ int gemm(bool beta, View A, View B, View C, int64_t m, int64_t n, int64_t k, voi
   const int smem = std::max(B_BYTES + NST * A_BYTES + SCR_BYTES + 1024, 116 * 1024);
   const int64_t tiles = ((m + BM - 1) / BM) * (z.Npad / Cfg<L>::N);
   const int grid = (int)std::min<int64_t>(tiles, sm_count());
-  if (k == 0) {  // nothing to multiply: C unchanged (beta) or zero
-    if (!beta) {
-      for (int pl = 0; pl < 2 * L; pl++) {
-        cudaError_t e = cudaMemset2DAsync(C.p + (int64_t)pl * C.ps, C.ld * sizeof(double), 0, m * sizeof(double), n, s);
-        if (e != cudaSuccess) return (int)e;
-      }
-    }
-    return 0;
-  }
   if (beta) {
     auto kern = k_oz_gemm<L, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

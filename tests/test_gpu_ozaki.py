@@ -5,7 +5,8 @@
 * ZGEMM (C = AB and C - AB): against the exact product (oracle
   superaccumulator) within the Ozaki bound
   2^(Ea_i + Eb_j) 2k 2^(-beta S) (L + S + 2) + 2^(2 - 53L) |result|;
-* LU with the Ozaki update: pivots identical to the oracle's, backward error
+* LU with the Ozaki update: pivots identical to the oracle's (no mismatch
+  accepted), backward error
   <= 16 n u; known-factor matrices reproduced bit for bit.
 """
 import numpy as np
@@ -118,8 +119,7 @@ def test_lu_ozaki_parity(api, orc, L, nb):
     LUo, ipo, _, gap = orc.zgetrf(A)
     ipg = host(ipiv)
     mism = np.nonzero(ipg != ipo)[0]
-    if mism.size:
-        assert gap[mism[0]] < 2.0 ** -(53 * L - 16)
+    assert mism.size == 0, ("pivots differ", mism[:4], ipg[mism[:4]], ipo[mism[:4]], gap[mism[:4]])
     xr, xi = inputs.ones_x_true(n)
     b = inputs.truncate_limbs(inputs.exact_rhs(A, xr, xi, L_out=4), L)
     x = host(api.lu_solve(LU, ipiv, dev(b)))
@@ -139,8 +139,7 @@ def test_lu_ozaki_parity_wide_block(api, orc, L):
     LUo, ipo, _, gap = orc.zgetrf(A)
     ipg = host(ipiv)
     mism = np.nonzero(ipg != ipo)[0]
-    if mism.size:
-        assert gap[mism[0]] < 2.0 ** -(53 * L - 16)
+    assert mism.size == 0, ("pivots differ", mism[:4], ipg[mism[:4]], ipo[mism[:4]], gap[mism[:4]])
     xr, xi = inputs.ones_x_true(n)
     b = inputs.truncate_limbs(inputs.exact_rhs(A, xr, xi, L_out=4), L)
     x = host(api.lu_solve(LU, ipiv, dev(b)))
@@ -163,8 +162,7 @@ def test_lu_ozaki_zero_column(api, orc, L, zc):
     assert int(host(info)[0]) == info_o == zc + 1
     ipg = host(ipiv)
     mism = np.nonzero(ipg != ipo)[0]
-    if mism.size:
-        assert gap[mism[0]] < 2.0 ** -(53 * L - 16)
+    assert mism.size == 0, ("pivots differ", mism[:4], ipg[mism[:4]], ipo[mism[:4]], gap[mism[:4]])
     diff = np.abs((host(LU) - LUo).sum(axis=1)).max()
     assert diff <= 2.0 ** 10 * n * 2.0 ** -U_EXP[L] * np.abs(A[:, 0]).max() * max(1.0, np.abs(LUo[:, 0]).max())
 

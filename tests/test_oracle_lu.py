@@ -9,6 +9,10 @@
 * ZGEMM 4M and 3M (Eq. 3) against exact entries, with the componentwise 4M
   bound and the normwise 3M bound; 3M and 4M agree within the sum of bounds.
 * Adjoint: lambda = A^{-H} xbar and Abar = -lambda x^H against exact rationals.
+* The per-step pivot-key gap the oracle records equals exact GEPP's; an
+  exact tie gives 0 and a constructed gap its value.
+* The exact P A - L U checker (orc_exact_entries in L U mode) gives 0 on
+  known factors and exactly the planted change after a one-ulp edit.
 """
 from fractions import Fraction
 
@@ -189,3 +193,91 @@ def test_zero_pivot_info(orc):
     M = exact.matrix(A)
     _, eipiv, einfo, _ = exact.gepp(M)
     assert einfo == 3 and list(ipiv) == eipiv
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+@pytest.mark.parametrize("n", [2, 5, 8])
+def test_pivot_gap_against_exact(orc, L, n):
+    """The oracle's per-step gap between the two largest pivot keys equals the
+    exact rational GEPP's relative gap (k1 - k2) / k1 to binary64 resolution,
+    at every step of the elimination (1 where fewer than two candidates)."""
+    A = inputs.gaussian_matrix(n, L, seed=140 + n + L)
+    _, ipiv, _, gap = orc.zgetrf(A)
+    _, eipiv, _, egaps = exact.gepp(exact.matrix(A))
+    assert list(ipiv) == eipiv
+    for k in range(n):
+        assert abs(gap[k] - float(egaps[k])) <= 2.0 ** -50, (k, gap[k], float(egaps[k]))
+    assert gap[n - 1] == 1.0
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_pivot_gap_tie_and_clear_gap(orc, L):
+    """Constructed first columns: an exact tie of the two largest cabs1 keys
+    (1 + 2i and -2 + 1i, both 3) gives gap 0 and the lower row; keys 4 and 3
+    give gap exactly 1/4; a zero column gives gap 1 (k1 = 0)."""
+    n = 5
+    A = inputs.gaussian_matrix(n, L, seed=150)
+    A[:, :, 0, :] = 0.0
+    col = [(0.5, 0.25), (1.0, 2.0), (0.25, -0.5), (-2.0, 1.0), (0.0, 1.0)]
+    for i, (re, im) in enumerate(col):
+        A[0, 0, 0, i], A[1, 0, 0, i] = re, im
+    _, ipiv, _, gap = orc.zgetrf(A)
+    assert ipiv[0] == 2 and gap[0] == 0.0           # tie: rows 1 and 3, the lower index wins
+    col = [(0.5, 0.25), (3.0, -1.0), (0.25, -0.5), (-2.0, 1.0), (0.0, 1.0)]
+    for i, (re, im) in enumerate(col):
+        A[0, 0, 0, i], A[1, 0, 0, i] = re, im
+    _, ipiv, _, gap = orc.zgetrf(A)
+    assert ipiv[0] == 2 and gap[0] == 0.25           # keys 4 (row 1) and 3 (row 3)
+    A[:, :, 0, :] = 0.0
+    _, ipiv, info, gap = orc.zgetrf(A)
+    assert info == 1 and ipiv[0] == 1 and gap[0] == 1.0
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_exact_entries_lower_unit_known_factors(orc, L):
+    """orc_exact_entries in its L U mode (unit lower L, upper U, both read from
+    one packed array): on known factors with P A = L U exactly it returns 0
+    at every position; after a one-ulp change of one entry of L (or of U) it
+    returns exactly the change times the matching row of U (column of L) at
+    the affected positions and 0 elsewhere."""
+    from fractions import Fraction
+    n = 12
+    A, ipiv, packed, _, _ = known_factor_case(n, L, seed=160)
+    P = np.arange(n)
+    for k, p in enumerate(ipiv - 1):
+        P[k], P[p] = P[p], P[k]
+    PA = np.ascontiguousarray(A[:, :, :, P])
+    rows, cols = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    rows, cols = rows.ravel(), cols.ravel()
+    d = orc.exact_entries(packed, packed, rows, cols, C=PA, sign=-1, lu=True)
+    assert np.all(d == 0.0)
+
+    def check(LU, expect):
+        d = orc.exact_entries(LU, LU, rows, cols, C=PA, sign=-1, lu=True)
+        for s, (i, j) in enumerate(zip(rows, cols)):
+            want = expect.get((int(i), int(j)), (Fraction(0), Fraction(0)))
+            got = tuple(sum((Fraction(float(v)) for v in d[s, c]), Fraction(0)) for c in range(2))
+            assert got == want, (i, j, got, want)
+
+    # L entry (r, q), r > q, raised by one ulp (real): P A - L U changes by -delta U[q, c] for c >= q
+    r, q = 9, 4
+    LU = packed.copy()
+    old = LU[0, 0, q, r]
+    LU[0, 0, q, r] = np.nextafter(old, np.inf)
+    delta = Fraction(float(LU[0, 0, q, r])) - Fraction(float(old))
+    assert delta != 0
+    expect = {(r, c): (-delta * Fraction(float(packed[0, 0, c, q])), -delta * Fraction(float(packed[1, 0, c, q])))
+              for c in range(q, n)}
+    check(LU, expect)
+    # U entry (q, c0), imaginary part, raised by one ulp: changes -L[i, q] * i delta for i >= q (L[q, q] = 1)
+    q, c0 = 3, 8
+    LU = packed.copy()
+    old = LU[1, 0, c0, q]
+    LU[1, 0, c0, q] = np.nextafter(old, np.inf)
+    delta = Fraction(float(LU[1, 0, c0, q])) - Fraction(float(old))
+    expect = {}
+    for i in range(q, n):
+        lr = Fraction(1) if i == q else Fraction(float(packed[0, 0, q, i]))
+        li = Fraction(0) if i == q else Fraction(float(packed[1, 0, q, i]))
+        expect[(i, c0)] = (li * delta, -lr * delta)   # -(lr + i li)(i delta) = li delta - i lr delta
+    check(LU, expect)
