@@ -11,7 +11,17 @@ The default step uses the Ozaki-scheme trailing update on the tensor cores
 (nb = 128, factored as four 32-column sub-panels); the same step with the
 plain FP64-pipe 4M update (nb = 64) is
 timed right after it and reported under "plain", with both backward errors,
-so that the speed-up is stated at equal accuracy.
+so that the speed-up is stated at equal accuracy.  The TD and QD steps (Ozaki
+and plain, n = 4096) follow under "precisions", and the standalone complex
+ZGEMM of m = n = k = 1024 (4M, 3M, Ozaki; DD, TD, QD) under "zgemm_1024".
+FP64-pipe rooflines use the FP64 rate measured in the same run
+(mclu_probe_fp64_rate) as their peak.
+
+Other modes (one JSON line per point): --sweep (block width, the paper's
+time-vs-K study), --slices-sweep (Ozaki slices per operand against accuracy,
+the paper's divisions study), --zgemm (standalone ZGEMM workloads: 1024^3 per
+precision with 3M against 4M, and 4096^3 DD / TD with entries spread over
+2^+-20, Ozaki against plain).
 
 Timing: W untimed warm-up steps, then K steps between a barrier +
 torch.cuda.synchronize() on both sides, CUDA events on the library's stream,
@@ -64,6 +74,14 @@ PANEL_TRAFFIC = {"dd": {"bytes": 2218240 + 36608, "m": 2048, "w": 32, "src_sha1"
 U_EXP = {"dd": 104, "td": 157, "qd": 209}
 
 
+def fp64_peak(measured: float | None) -> tuple[float, str]:
+    """FP64 operations per second for the alu rooflines: the rate measured in
+    this run by mclu_probe_fp64_rate, else the nominal figure."""
+    if measured:
+        return measured, "measured FP64 DFMA rate (mclu_probe_fp64_rate, this run)"
+    return FP64_OPS_PEAK, "nominal FP64 (1.25 TFLOP/s, FMA = 2)"
+
+
 def measured_bf16_peak() -> tuple[float, str]:
     """Dense bf16 TFLOP/s from MEASURED_PEAKS.json (burst), else the fallback."""
     try:
@@ -87,6 +105,12 @@ def parse():
     p.add_argument("--no-plain", action="store_true", help="skip the plain 4M comparison of an ozaki run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle sample")
+    p.add_argument("--slices", type=int, default=0, help="Ozaki slices per operand (0: the precision's default)")
+    p.add_argument("--no-precisions", action="store_true", help="skip the TD / QD steps of the default line")
+    p.add_argument("--no-zgemm", action="store_true", help="skip the 1024^3 ZGEMM sub-object of the default line")
+    p.add_argument("--slices-sweep", action="store_true",
+                   help="LU + solve GFLOP/s and backward error against the Ozaki slice count, per precision")
+    p.add_argument("--zgemm", action="store_true", help="standalone ZGEMM workloads, one JSON line per point")
     p.add_argument("--sweep", action="store_true",
                    help="block-width sweep instead of the benchmark line: LU + solve GFLOP/s for every method "
                         "and nb at --n (default 1024), plus the unblocked form; one JSON line per point")
@@ -238,7 +262,8 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def panel_roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el_ms: float):
+def panel_roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el_ms: float,
+                   fp64: float | None = None):
     """Roofline of the cooperative panel kernel (FP64 pipe): the algorithmic
     FP64 operations of its multipliers and rank-1 updates (4 real
     product-accumulates of I_REAL operations per complex multiply-accumulate)
@@ -265,15 +290,17 @@ def panel_roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: di
                 rows = [n - s0 for s0 in range(0, n, w)]
                 traffic = cap["bytes"] * (sum(rows) / len(rows)) / cap["m"]
                 note = "ncu dram read+write of one launch with m = 2048 rows, scaled to the average launch by rows"
-    return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "T FP64-ops/s",
-            "frac": achieved / FP64_OPS_PEAK, "peak_source": "nominal FP64 (1.25 TFLOP/s, FMA = 2)",
+    peak, src = fp64_peak(fp64)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T FP64-ops/s",
+            "frac": achieved / peak, "peak_source": src,
             "traffic": traffic, "traffic_note": note,
             "kernel": f"{'k_panel_coop' if LIMBS[prec] == 2 else 'k_panel_team'}<{LIMBS[prec]}> "
                       "(latency bound: a serial FP64 chain per column)",
             "ops_per_launch": per_launch, "avg_launch_ms": panel_ms / panel_calls, "share_of_step": panel_ms / el_ms}
 
 
-def roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el_ms: float):
+def roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el_ms: float,
+             fp64: float | None = None, slices: int = 0):
     """Roofline of the trailing update: algorithmic work per launch (from n, nb
     and the method) over its average event-timed duration."""
     L = LIMBS[prec]
@@ -281,7 +308,7 @@ def roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el
     if not gemm_calls:
         return None
     if method == "ozaki":
-        S = OZAKI_S[prec]
+        S = slices or OZAKI_S[prec]
         pairs = S * (S + 1) // 2
         # realified real GEMM per kept slice pair: n2 x (2 n2) x (2 jb), 2 flops per MAC
         flops = 0.0
@@ -294,7 +321,7 @@ def roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el
         peak, src = measured_bf16_peak()
         traffic = None
         cap = OZ_TRAFFIC.get(prec)
-        if cap and nb == 128 and n == 4096:
+        if cap and nb == 128 and n == 4096 and S == OZAKI_S[prec]:
             import hashlib
             with open(os.path.join(ROOT, "paper_2403_16013_gb300", "csrc", "ozaki.cuh"), "rb") as f:
                 if hashlib.sha1(f.read()).hexdigest() == cap["src_sha1"]:
@@ -317,8 +344,9 @@ def roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el
         per_mac = (3 if method == "3m" else 4) * I_REAL[prec]
         per_launch_ops = macs * per_mac / (gemm_calls / steps)
         achieved = per_launch_ops / (gemm_ms / gemm_calls * 1e-3)
-        return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "T FP64-ops/s",
-                "frac": achieved / FP64_OPS_PEAK, "peak_source": "nominal FP64 (1.25 TFLOP/s, FMA = 2)",
+        peak, src = fp64_peak(fp64)
+        return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T FP64-ops/s",
+                "frac": achieved / peak, "peak_source": src,
                 "traffic": None, "kernel": f"k_gemm<{L},{'3M' if method == '3m' else '4M'},beta>",
                 "ops_per_launch": per_launch_ops, "avg_launch_ms": gemm_ms / gemm_calls,
                 "share_of_step": gemm_ms / el_ms}
@@ -326,15 +354,15 @@ def roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el
 
 
 def backward_error(api, A0, X, B0):
-    """||b - A x||_inf / (||A||_inf ||x||_inf) (modulus norms).  The residual is
-    formed by the library's QD ZGEMM on the limbs zero-padded to four, which
-    resolves it far below the bound for DD and TD.  A QD residual lies below
-    the resolution of a four-limb accumulation, so for QD None is returned
-    (the tests check it with the exact residual)."""
+    """||b - A x||_inf / (||A||_inf ||x||_inf) (modulus norms), the residual
+    formed by the library's ZGEMM (both forms tested against the exact product):
+    DD and TD with the QD 4M product on the limbs zero-padded to four, which
+    resolves it far below the bound; QD with the QD Ozaki product, whose
+    C - A B epilogue is exact and whose slice truncation stays below
+    2^-204 max|A_i.| max|x| (about 2^-216 of ||A|| ||x|| at n = 4096), below
+    a QD residual."""
     import torch
     L = A0.shape[1]
-    if L == 4:
-        return None
 
     def pad(T):
         if L == 4:
@@ -343,11 +371,15 @@ def backward_error(api, A0, X, B0):
         P[:, :L] = T
         return P
 
-    R = api.zgemm(pad(A0), pad(X), C=pad(B0))
-    r = torch.hypot(R[0, 0], R[1, 0]).max().item()
+    R = api.zgemm(pad(A0), pad(X), C=pad(B0), method="ozaki" if L == 4 else "4m")
+    r = torch.hypot(R[0].sum(dim=0), R[1].sum(dim=0)).max().item()
     anorm = torch.hypot(A0[0, 0], A0[1, 0]).sum(dim=0).max().item()
     xnorm = torch.hypot(X[0, 0], X[1, 0]).max().item()
     return r / (anorm * xnorm)
+
+
+RESIDUAL_NOTE = ("b - A x by the library's ZGEMM: QD 4M on zero-padded limbs (DD, TD), QD Ozaki with its exact "
+                 "C - A B epilogue (QD)")
 
 
 def run_sweep(args):
@@ -390,6 +422,192 @@ def run_sweep(args):
                           "info": int(info.item())}), flush=True)
 
 
+def lu_step_fn(api, A, A0, x, b0, ipiv, info, method, nb, slices):
+    def step():
+        A.copy_(A0)
+        api.lu_factor_(A, ipiv, info, method=method, nb=nb, ozaki_slices=slices if method == "ozaki" else 0)
+        x.copy_(b0)
+        api.lu_solve(A, ipiv, x, inplace=True)
+    return step
+
+
+def time_lu(ctx, prec, method, nb, steps, warmup, slices=0, sampler=None, ws=1, stream=None, fp64=None,
+            warm_n=0):
+    """LU + solve of the prec's benchmark matrix: warm-up steps (at order warm_n
+    when given, which loads the kernels without the cost of full-size steps),
+    then `steps` steps between barriers and CUDA events on the library's stream,
+    with launch-class timing; returns value, phases, rooflines, backward error."""
+    import torch
+    api, binding = ctx["api"], ctx["binding"]
+    n = ctx["n"]
+    A0, b0 = ctx["inputs"][prec]
+    A, x = torch.empty_like(A0), torch.empty_like(b0)
+    ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    step = lu_step_fn(api, A, A0, x, b0, ipiv, info, method, nb, slices)
+    if warm_n:
+        Aw = A0[:, :, :warm_n, :warm_n].contiguous()
+        bw = b0[:, :, :, :warm_n].contiguous()
+        Ax, xw = torch.empty_like(Aw), torch.empty_like(bw)
+        ipw = torch.empty(warm_n, dtype=torch.int32, device="cuda")
+        wstep = lu_step_fn(api, Ax, Aw, xw, bw, ipw, info, method, nb, slices)
+        for _ in range(max(1, warmup)):
+            wstep()
+    else:
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize()
+    if int(info.item()) != 0:
+        raise RuntimeError(f"zgetrf info {int(info.item())} on the benchmark matrix")
+    barrier(ws)
+    torch.cuda.synchronize()
+    if sampler is not None:
+        sampler.start()
+        time.sleep(0.4)
+    binding.profile_begin(("gemm", "panel", "trsm", "laswp", "getrs", "other"))
+    launches0 = binding.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = binding.launch_count() - launches0
+    prof = binding.profile_end()
+    clocks = sampler.stop() if sampler is not None else None
+    el_ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    if int(info.item()) != 0:
+        raise RuntimeError(f"zgetrf info {int(info.item())} on the benchmark matrix")
+    upd = roofline(method, prec, n, nb, steps, prof, el_ms, fp64=fp64, slices=slices)
+    pan = panel_roofline(method, prec, n, nb, steps, prof, el_ms, fp64=fp64)
+    # the "roofline" object describes the kernel with the largest share of the step
+    first, second = (pan, upd) if (pan and (not upd or pan["share_of_step"] > upd["share_of_step"])) else (upd, pan)
+    eta = backward_error(api, A0, x, b0)
+    return {"el_ms": el_ms, "launches": launches, "prof": prof, "clocks": clocks, "steps": steps,
+            "warmup": warmup, "value": job_throughput(ws, steps, 8.0 * n ** 3 / 3.0, el_ms),
+            "backward_error": eta, "roofline": first, "roofline_secondary": second,
+            "ipiv": ipiv}
+
+
+def sub_object(r: dict, method: str, nb: int, slices: int, prec: str, n: int) -> dict:
+    out = {"method": method, "nb": nb, "value": r["value"], "unit": "GFLOP/s", "ms_per_step": r["el_ms"] / r["steps"],
+           "steps": r["steps"], "warmup": r["warmup"], "backward_error": r["backward_error"],
+           "bound_16nu": 16.0 * n * 2.0 ** -U_EXP[prec], "roofline": r["roofline"],
+           "roofline_secondary": r["roofline_secondary"],
+           "phases_ms_per_step": {k: v[0] / r["steps"] for k, v in r["prof"].items()}}
+    if method == "ozaki":
+        out["ozaki_slices"] = slices or OZAKI_S[prec]
+    return out
+
+
+def zgemm_point(ctx, prec, method, m, n, k, reps, A, B, fp64=None, slices=0) -> dict:
+    """Standalone C = A B (beta_mode 0): ms per call (CUDA events, after one
+    warm-up call), GFLOP/s counted as 8 m n k, and the roofline of the kernel."""
+    import torch
+    api, binding = ctx["api"], ctx["binding"]
+    api.zgemm(A, B, method=method, ozaki_slices=slices)
+    torch.cuda.synchronize()
+    binding.profile_begin(("gemm",))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        C = api.zgemm(A, B, method=method, ozaki_slices=slices)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = binding.profile_end()
+    del C
+    ms = e0.elapsed_time(e1) / reps
+    kern_ms = prof["gemm"][0] / max(1, prof["gemm"][1])
+    L = LIMBS[prec]
+    out = {"prec": prec, "method": method, "m": m, "n": n, "k": k, "ms": ms, "value": 8.0 * m * n * k / (ms * 1e-3) / 1e9,
+           "unit": "GFLOP/s"}
+    if method == "ozaki":
+        S = slices or OZAKI_S[prec]
+        flops = S * (S + 1) // 2 * 2.0 * m * (2 * n) * (2 * k)
+        peak, src = measured_bf16_peak()
+        ach = flops / (kern_ms * 1e-3) / 1e12
+        out["ozaki_slices"] = S
+        out["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                           "peak_source": src + " bf16 burst", "traffic": None,
+                           "kernel": f"k_oz_gemm<{L},0> (+ split kernels)"}
+    else:
+        ops = float(m) * n * k * (3 if method == "3m" else 4) * I_REAL[prec]
+        peak, src = fp64_peak(fp64)
+        ach = ops / (kern_ms * 1e-3)
+        out["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T FP64-ops/s",
+                           "frac": ach / peak, "peak_source": src, "traffic": None,
+                           "kernel": f"k_gemm<{L},{'3M' if method == '3m' else '4M'},0> (+ k_resum for 3M)"}
+    return out
+
+
+def setup(args, precs):
+    import torch
+    from paper_2403_16013_gb300 import api, binding, build
+    build.build()
+    binding.load()
+    ctx = {"api": api, "binding": binding, "n": args.n, "inputs": {}}
+    for prec in precs:
+        A_h, b_h = make_inputs(args.n, LIMBS[prec])
+        ctx["inputs"][prec] = (torch.from_numpy(A_h).cuda(), torch.from_numpy(b_h).cuda())
+    return ctx
+
+
+def run_slices_sweep(args):
+    """The paper's divisions study (Sec. 4.1-4.3: how many Ozaki divisions each
+    precision needs inside LU) on this engine: for each precision, LU + solve
+    at --n with S, S-1, ... slices per operand, the backward error of each,
+    and the plain 4M step's, one JSON line per point."""
+    import torch
+    torch.cuda.set_device(0)
+    precs = [args.prec] if args.prec != "dd" or args.n != 4096 else ["dd", "td", "qd"]
+    for prec in precs:
+        ctx = setup(args, [prec])
+        n = args.n
+        plain = time_lu(ctx, prec, "4m", 64, 1, 1, warm_n=256)
+        print(json.dumps({"slices_sweep": True, "prec": prec, "n": n, "method": "4m", "value": plain["value"],
+                          "ms_per_step": plain["el_ms"], "backward_error": plain["backward_error"]}), flush=True)
+        S = OZAKI_S[prec]
+        for Se in range(S, max(1, S - 8), -1):
+            r = time_lu(ctx, prec, "ozaki", 128, max(1, args.steps), 1, slices=Se)
+            same = bool(torch.equal(r["ipiv"], plain["ipiv"]))
+            print(json.dumps({"slices_sweep": True, "prec": prec, "n": n, "method": "ozaki", "ozaki_slices": Se,
+                              "value": r["value"], "ms_per_step": r["el_ms"] / r["steps"],
+                              "backward_error": r["backward_error"],
+                              "eta_over_plain": r["backward_error"] / plain["backward_error"],
+                              "bound_16nu": 16.0 * n * 2.0 ** -U_EXP[prec], "pivots_equal_plain": same}),
+                  flush=True)
+        del ctx
+        torch.cuda.empty_cache()
+
+
+def run_zgemm(args):
+    """Standalone ZGEMM workloads: m = n = k = 1024 per precision, 4M / 3M /
+    Ozaki on Gaussian limbs (seeds 1, 2); m = n = k = 4096 DD and TD with
+    entries N(0,1) 2^e, e in [-20, 20] (seeds 3, 4), Ozaki against 4M."""
+    import torch
+    from paper_2403_16013_gb300 import inputs
+    torch.cuda.set_device(0)
+    ctx = setup(args, [])
+    fp64 = ctx["binding"].probe_fp64_rate()
+    for prec in ("dd", "td", "qd"):
+        L = LIMBS[prec]
+        A = torch.from_numpy(inputs.gaussian_matrix(1024, L, seed=1)).cuda()
+        B = torch.from_numpy(inputs.gaussian_matrix(1024, L, seed=2)).cuda()
+        for method in ("4m", "3m", "ozaki"):
+            r = zgemm_point(ctx, prec, method, 1024, 1024, 1024, max(1, args.steps), A, B, fp64=fp64)
+            r["workload"] = "gaussian limbs 1024^3"
+            print(json.dumps(r), flush=True)
+    for prec in ("dd", "td"):
+        L = LIMBS[prec]
+        A = torch.from_numpy(inputs.spread_matrix(4096, 4096, L, seed=3, spread=20)).cuda()
+        B = torch.from_numpy(inputs.spread_matrix(4096, 4096, L, seed=4, spread=20)).cuda()
+        for method in ("ozaki", "4m"):
+            r = zgemm_point(ctx, prec, method, 4096, 4096, 4096, 1, A, B, fp64=fp64)
+            r["workload"] = "exponent spread 2^+-20, 4096^3"
+            print(json.dumps(r), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -398,67 +616,28 @@ def main():
     if args.sweep:
         run_sweep(args)
         return
+    if args.slices_sweep:
+        run_slices_sweep(args)
+        return
+    if args.zgemm:
+        run_zgemm(args)
+        return
     import torch
 
     ws, rank, local = dist_init()
     torch.cuda.set_device(local)
-    from paper_2403_16013_gb300 import api, binding, build
-    build.build()
-    binding.load()
     n, L, prec = args.n, LIMBS[args.prec], args.prec
+    others = [] if (args.no_precisions or args.prec != "dd") else ["td", "qd"]
+    ctx = setup(args, [prec])
+    api, binding = ctx["api"], ctx["binding"]
+    fp64 = binding.probe_fp64_rate()
     nb_of = lambda m: args.nb if args.nb else (128 if m == "ozaki" else 64)
-    A_h, b_h = make_inputs(n, L)
-    A0 = torch.from_numpy(A_h).cuda()
-    b0 = torch.from_numpy(b_h).cuda()
-    A = torch.empty_like(A0)
-    x = torch.empty_like(b0)
-    ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
-    info = torch.zeros(1, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
-    flops = 8.0 * n ** 3 / 3.0
-
-    def timed(method: str, nb: int, sampler=None) -> dict:
-        def step():
-            A.copy_(A0)
-            api.lu_factor_(A, ipiv, info, method=method, nb=nb)
-            x.copy_(b0)
-            api.lu_solve(A, ipiv, x, inplace=True)
-
-        for _ in range(args.warmup):
-            step()
-        torch.cuda.synchronize()
-        if int(info.item()) != 0:
-            raise RuntimeError(f"zgetrf info {int(info.item())} on the benchmark matrix")
-        barrier(ws)
-        torch.cuda.synchronize()
-        if sampler is not None:
-            sampler.start()
-            time.sleep(0.4)
-        binding.profile_begin(("gemm", "panel", "trsm", "laswp", "getrs", "other"))
-        launches0 = binding.launch_count()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier(ws)
-        launches = binding.launch_count() - launches0
-        prof = binding.profile_end()
-        clocks = sampler.stop() if sampler is not None else None
-        el_ms = max_over_ranks(e0.elapsed_time(e1), ws)
-        upd = roofline(method, prec, n, nb, args.steps, prof, el_ms)
-        pan = panel_roofline(method, prec, n, nb, args.steps, prof, el_ms)
-        # the "roofline" object describes the kernel with the largest share of the step
-        first, second = (pan, upd) if (pan and (not upd or pan["share_of_step"] > upd["share_of_step"])) else (upd, pan)
-        return {"el_ms": el_ms, "launches": launches, "prof": prof, "clocks": clocks,
-                "value": job_throughput(ws, args.steps, flops, el_ms),
-                "backward_error": backward_error(api, A0, x, b0),
-                "roofline": first, "roofline_secondary": second}
-
     method, nb = args.method, nb_of(args.method)
-    main_run = timed(method, nb, ClockSampler(local))
+    main_run = time_lu(ctx, prec, method, nb, args.steps, args.warmup, slices=args.slices,
+                       sampler=ClockSampler(local), ws=ws, stream=stream, fp64=fp64)
     bound = 16.0 * n * 2.0 ** -U_EXP[prec]
+    A_bytes = ctx["inputs"][prec][0].numel() * 8
     line = {"metric": "complex DD/TD/QD LU GFLOPS (8n^3/3/t) at n=4096", "value": main_run["value"],
             "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": main_run["el_ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -466,33 +645,39 @@ def main():
             "config": {"workload": f"complex {prec.upper()} LU (zgetrf, partial pivoting) + solve (zgetrs), n={n}, "
                                    f"nb={nb}, {method.upper()} trailing update, Gaussian limbs seed 1",
                        "n": n, "prec": prec, "method": method, "nb": nb,
-                       "l2": "inputs larger than L2 (%.0f MB per matrix), no flush" % (A_h.nbytes / 1e6),
+                       "l2": "inputs larger than L2 (%.0f MB per matrix), no flush" % (A_bytes / 1e6),
                        "parallelism": f"replicas x{ws}"},
             "gpu_launches": main_run["launches"], "clocks": main_run["clocks"], "roofline": main_run["roofline"],
             "roofline_secondary": main_run["roofline_secondary"],
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in main_run["prof"].items()},
             "accuracy": {"backward_error": main_run["backward_error"], "bound_16nu": bound,
-                         "residual": "b - A x by the library's QD ZGEMM" if L < 4 else
-                         "not resolvable in four limbs; exact check in the tests"}}
+                         "residual": RESIDUAL_NOTE},
+            "fp64_measured_ops_per_s": fp64}
+    if method == "ozaki":
+        line["config"]["ozaki_slices"] = args.slices or OZAKI_S[prec]
 
     if method == "ozaki" and not args.no_plain:
         # the same step with the plain FP64-pipe 4M update, for the speed-up at equal accuracy
-        plain = timed("4m", args.nb if args.nb else 64)
-        line["plain"] = {"method": "4m", "nb": args.nb if args.nb else 64, "value": plain["value"],
-                         "unit": "GFLOP/s", "ms_per_step": plain["el_ms"] / args.steps,
-                         "backward_error": plain["backward_error"], "roofline": plain["roofline"],
-                         "phases_ms_per_step": {k: v[0] / args.steps for k, v in plain["prof"].items()}}
+        plain = time_lu(ctx, prec, "4m", nb_of("4m"), min(args.steps, 5), min(args.warmup, 2), ws=ws,
+                        stream=stream, fp64=fp64)
+        line["plain"] = sub_object(plain, "4m", nb_of("4m"), 0, prec, n)
         line["ozaki_speedup_vs_plain"] = main_run["value"] / plain["value"]
 
     if not args.no_e2e:
+        A_h = ctx["inputs"][prec][0].cpu().numpy()
+        b_h = ctx["inputs"][prec][1].cpu().numpy()
         A_pin = torch.from_numpy(A_h).pin_memory()
         b_pin = torch.from_numpy(b_h).pin_memory()
         x_pin = torch.empty_like(b_pin).pin_memory()
         ipiv_pin = torch.empty(n, dtype=torch.int32).pin_memory()
+        A = torch.empty_like(ctx["inputs"][prec][0])
+        x = torch.empty_like(ctx["inputs"][prec][1])
+        ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
 
         def e2e_step():
             A.copy_(A_pin, non_blocking=True)
-            api.lu_factor_(A, ipiv, info, method=method, nb=nb)
+            api.lu_factor_(A, ipiv, info, method=method, nb=nb, ozaki_slices=args.slices if method == "ozaki" else 0)
             x.copy_(b_pin, non_blocking=True)
             api.lu_solve(A, ipiv, x, inplace=True)
             x_pin.copy_(x, non_blocking=True)
@@ -508,9 +693,35 @@ def main():
         torch.cuda.synchronize()
         barrier(ws)
         el = max_over_ranks(time.perf_counter() - t0, ws)
-        line["e2e"] = {"value": job_throughput(ws, max(1, args.steps), flops, el * 1e3), "unit": "GFLOP/s",
-                       "h2d_bytes_per_step": A_h.nbytes + b_h.nbytes,
+        line["e2e"] = {"value": job_throughput(ws, max(1, args.steps), 8.0 * n ** 3 / 3.0, el * 1e3),
+                       "unit": "GFLOP/s", "h2d_bytes_per_step": A_h.nbytes + b_h.nbytes,
                        "d2h_bytes_per_step": b_h.nbytes + 4 * n}
+        del A, x, A_pin
+
+    if others:
+        # TD and QD at the same order: the Ozaki step (3 warm-up, up to 5 timed) and the plain 4M
+        # step (warmed up at n = 256, one timed step: 7-20 s each at n = 4096)
+        del ctx["inputs"][prec]
+        line["precisions"] = {}
+        for p2 in others:
+            ctx2 = setup(args, [p2])
+            oz = time_lu(ctx2, p2, "ozaki", 128, min(args.steps, 5), 3, ws=ws, stream=stream, fp64=fp64)
+            pl = time_lu(ctx2, p2, "4m", 64, 1, 1, ws=ws, stream=stream, fp64=fp64, warm_n=256)
+            line["precisions"][p2] = {"ozaki": sub_object(oz, "ozaki", 128, 0, p2, n),
+                                      "plain": sub_object(pl, "4m", 64, 0, p2, n),
+                                      "ozaki_speedup_vs_plain": oz["value"] / pl["value"]}
+            del ctx2
+            torch.cuda.empty_cache()
+
+    if not args.no_zgemm:
+        from paper_2403_16013_gb300 import inputs
+        line["zgemm_1024"] = []
+        for p2 in ("dd", "td", "qd"):
+            L2 = LIMBS[p2]
+            Ag = torch.from_numpy(inputs.gaussian_matrix(1024, L2, seed=1)).cuda()
+            Bg = torch.from_numpy(inputs.gaussian_matrix(1024, L2, seed=2)).cuda()
+            for m2 in ("4m", "3m", "ozaki"):
+                line["zgemm_1024"].append(zgemm_point(ctx, p2, m2, 1024, 1024, 1024, 2, Ag, Bg, fp64=fp64))
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prec, args.cpu_seconds)

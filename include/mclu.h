@@ -55,7 +55,8 @@ typedef struct mclu_opts {
   int32_t nb;           /* panel width K of Sec. 3 (block size NDIM); 0 = 64 (128 for Ozaki); */
                         /*   1..256                                                           */
   int32_t method;       /* MCLU_METHOD_*; default MCLU_METHOD_4M                             */
-  int32_t ozaki_slices; /* MCLU_METHOD_OZAKI: 0 or the precision's S (14 DD, 24 TD, 32 QD)      */
+  int32_t ozaki_slices; /* MCLU_METHOD_OZAKI: slices kept per operand, 1..S (S = 14 DD, 24 TD, */
+                        /*   32 QD; above S: MCLU_ERR_UNSUPPORTED); 0 = the precision's S     */
   int32_t reserved;     /* must be 0                                                          */
 } mclu_opts;
 
@@ -146,6 +147,24 @@ int zgemm_qd(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const d
              const double *B, int64_t ldb, double *C, int64_t ldc, void *stream);
 
 /*
+ * zgemm_{dd,td,qd}_ex: zgemm_* with the number of Ozaki slices (Sec. 2.3:
+ * the number of divisions of each operand, which sets the accuracy of the
+ * Ozaki-scheme product).
+ *   ozaki_slices  MCLU_METHOD_OZAKI: 1..S slices kept per operand (S = 14
+ *                 DD, 24 TD, 32 QD), the digit pairs p + q <= ozaki_slices - 1
+ *                 multiplied; 0 = S; above S: MCLU_ERR_UNSUPPORTED.  Ignored
+ *                 by the other methods.
+ *   the other arguments as in zgemm_* (argument errors are reported by
+ *   their position in this signature).
+ */
+int zgemm_dd_ex(int beta_mode, int method, int ozaki_slices, int64_t m, int64_t n, int64_t k, const double *A,
+                int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc, void *stream);
+int zgemm_td_ex(int beta_mode, int method, int ozaki_slices, int64_t m, int64_t n, int64_t k, const double *A,
+                int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc, void *stream);
+int zgemm_qd_ex(int beta_mode, int method, int ozaki_slices, int64_t m, int64_t n, int64_t k, const double *A,
+                int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc, void *stream);
+
+/*
  * zadjoint_rank1_{dd,td,qd}: Abar = -lambda x^H, the matrix part of the
  * adjoint of x = A^{-1} b (for lambda = A^{-H} xbar, computed by
  * zgetrs_*('C', ...); the right-hand-side part is bbar = lambda).
@@ -219,6 +238,19 @@ const char *mclu_status_string(int status);
 
 /* Library version as "major.minor.patch". */
 const char *mclu_version(void);
+
+/*
+ * mclu_probe_fp64_rate: measures the current device's FP64 throughput (a
+ * diagnostic for rooflines): 4 CTAs of 256 threads per SM, each thread 8
+ * independent chains of 40000 fused multiply-adds, timed with CUDA events on
+ * a stream of its own after a warm-up launch.  Writes to *ops_per_second
+ * (host) the FP64 instructions per second, one DFMA counted as one operation
+ * (the unit in which the library's kernels are costed: DADD, DMUL and DFMA
+ * are one operation each).  Allocates and frees 8 bytes of device memory and
+ * synchronises its stream (about 0.1 s on GB300).  Returns 0, -1 for a NULL
+ * pointer, or a CUDA error code.
+ */
+int mclu_probe_fp64_rate(double *ops_per_second);
 
 /*
  * mclu_selftest_wait_timeout: runs, on the current device, the bounded wait

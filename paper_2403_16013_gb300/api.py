@@ -69,16 +69,18 @@ def lu_solve(LU: torch.Tensor, ipiv: torch.Tensor, Bm: torch.Tensor, trans: str 
     return X
 
 
-def zgemm(A: torch.Tensor, Bm: torch.Tensor, C: torch.Tensor | None = None, method: str = "4m"):
-    """C = A B (C is None) or C - A B (returns a new tensor)."""
+def zgemm(A: torch.Tensor, Bm: torch.Tensor, C: torch.Tensor | None = None, method: str = "4m",
+          ozaki_slices: int = 0):
+    """C = A B (C is None) or C - A B (returns a new tensor).  ozaki_slices:
+    slices kept per operand by the Ozaki method (0 = the precision's S)."""
     _check_planes(A, "A")
     _check_planes(Bm, "B")
     k, m = A.shape[2], A.shape[3]
     n, ldb = Bm.shape[2], Bm.shape[3]
     beta = 0 if C is None else 1
     out = torch.zeros((2, A.shape[1], n, m), dtype=torch.float64, device=A.device) if C is None else C.clone()
-    rc = B.zgemm(_prec(A), beta, METHODS[method], m, n, k, A.data_ptr(), m, Bm.data_ptr(), ldb, out.data_ptr(),
-                 out.shape[3], _stream())
+    rc = B.zgemm_ex(_prec(A), beta, METHODS[method], ozaki_slices, m, n, k, A.data_ptr(), m, Bm.data_ptr(), ldb,
+                    out.data_ptr(), out.shape[3], _stream())
     B.check(rc, "zgemm")
     return out
 

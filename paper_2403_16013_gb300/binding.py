@@ -36,6 +36,8 @@ def _declare(lib):
         f.argtypes, f.restype = [cc, i64, i64, vp, i64, vp, vp, i64, vp], ci
         f = getattr(lib, f"zgemm_{s}")
         f.argtypes, f.restype = [ci, ci, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp], ci
+        f = getattr(lib, f"zgemm_{s}_ex")
+        f.argtypes, f.restype = [ci, ci, ci, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp], ci
         f = getattr(lib, f"zadjoint_rank1_{s}")
         f.argtypes, f.restype = [i64, vp, vp, vp, i64, vp], ci
         f = getattr(lib, f"zozaki_split_{s}")
@@ -46,6 +48,7 @@ def _declare(lib):
     lib.mclu_status_string.argtypes, lib.mclu_status_string.restype = [ci], C.c_char_p
     lib.mclu_version.argtypes, lib.mclu_version.restype = [], C.c_char_p
     lib.mclu_selftest_wait_timeout.argtypes, lib.mclu_selftest_wait_timeout.restype = [C.POINTER(C.c_int32)], ci
+    lib.mclu_probe_fp64_rate.argtypes, lib.mclu_probe_fp64_rate.restype = [C.POINTER(C.c_double)], ci
     lib.mclu_launch_count.argtypes, lib.mclu_launch_count.restype = [], C.c_uint64
     lib.mclu_profile_begin.argtypes, lib.mclu_profile_begin.restype = [C.c_uint32], ci
     lib.mclu_profile_end.argtypes, lib.mclu_profile_end.restype = [C.POINTER(C.c_double),
@@ -96,6 +99,13 @@ def selftest_wait_timeout() -> int:
     return int(st.value)
 
 
+def probe_fp64_rate() -> float:
+    """mclu_probe_fp64_rate: measured FP64 instructions per second of the current device."""
+    v = C.c_double(0.0)
+    check(load().mclu_probe_fp64_rate(C.byref(v)), "mclu_probe_fp64_rate")
+    return float(v.value)
+
+
 def status_string(rc: int) -> str:
     return load().mclu_status_string(rc).decode()
 
@@ -130,6 +140,11 @@ def zgetrs(prec: str, trans: str, n, nrhs, A, lda, ipiv, B, ldb, stream=None) ->
 
 def zgemm(prec: str, beta_mode, method, m, n, k, A, lda, B, ldb, Cm, ldc, stream=None) -> int:
     return getattr(load(), f"zgemm_{prec}")(beta_mode, method, m, n, k, A, lda, B, ldb, Cm, ldc, _stream(stream))
+
+
+def zgemm_ex(prec: str, beta_mode, method, ozaki_slices, m, n, k, A, lda, B, ldb, Cm, ldc, stream=None) -> int:
+    return getattr(load(), f"zgemm_{prec}_ex")(beta_mode, method, ozaki_slices, m, n, k, A, lda, B, ldb, Cm, ldc,
+                                               _stream(stream))
 
 
 def zadjoint_rank1(prec: str, n, lam, x, Abar, ldab, stream=None) -> int:

@@ -231,6 +231,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   if (lda < std::max<int64_t>(1, n)) return -3;
   if (n > 0 && ipiv == nullptr) return -4;
   int nb = 64, method = MCLU_METHOD_4M;
+  int Se = 0;  // Ozaki slices per operand (0: the precision's default)
   if (opts) {
     if (opts->nb < 0 || opts->nb > 256) return -6;
     if (opts->nb) nb = opts->nb;
@@ -238,10 +239,13 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     method = opts->method;
     if (opts->reserved != 0) return -6;
     if (method == MCLU_METHOD_OZAKI) {
-      if (opts->ozaki_slices != 0 && opts->ozaki_slices != oz::Cfg<L>::S) return MCLU_ERR_UNSUPPORTED;
+      if (opts->ozaki_slices < 0) return -6;
+      if (opts->ozaki_slices > oz::Cfg<L>::S) return MCLU_ERR_UNSUPPORTED;
+      Se = opts->ozaki_slices;
       if (opts->nb == 0) nb = 4 * oz::NB_MAX;  // 128: measured best at n = 4096 (64: -3%, 96: -1.3% DD)
     }
   }
+  if (Se == 0) Se = oz::default_slices<L>();
   if (n > INT32_MAX - 1) return -1;
   if (n == 0) {
     if (info) MCLU_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
@@ -355,7 +359,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
           if (rc) return rc;
           rc = oz::gemm<L>(true, View{Ap + s0 * lda + send, lda, lda * n}, View{Ap + send * lda + s0, lda, lda * n},
                            View{Ap + send * lda + send, lda, lda * n}, n - send, jend - send, sb, oz_ws, oz_status, s,
-                           note_launch);
+                           note_launch, Se);
           if (rc) return rc;
         }
       }
@@ -402,15 +406,15 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
                 View Pi{W.p + a * W.ld + a, W.ld, W.ps};
                 View Qi{W.p + (a + h) * W.ld + (a + h), W.ld, W.ps};
                 View X21{W.p + a * W.ld + (a + h), W.ld, W.ps};
-                int rc1 = oz::gemm<L>(false, Cv, Pi, Tm, hb, h, h, oz_ws, oz_status, s, note_launch);
+                int rc1 = oz::gemm<L>(false, Cv, Pi, Tm, hb, h, h, oz_ws, oz_status, s, note_launch, Se);
                 if (rc1) return rc1;
-                rc1 = oz::gemm<L>(true, Qi, Tm, X21, hb, h, hb, oz_ws, oz_status, s, note_launch);
+                rc1 = oz::gemm<L>(true, Qi, Tm, X21, hb, h, hb, oz_ws, oz_status, s, note_launch, Se);
                 if (rc1) return rc1;
               }
             }
           }
           int rc = oz::gemm<L>(false, W, View{Ap + jend * lda + j0, lda, lda * n}, View{Ap + jend * lda + j0, lda, lda * n},
-                               jb, n2, jb, oz_ws, oz_status, s, note_launch);
+                               jb, n2, jb, oz_ws, oz_status, s, note_launch, Se);
           if (rc) return rc;
         }
       }
@@ -429,7 +433,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
         if (rc) return rc;
       }
       ProfScope ps(PK_GEMM, s);
-      int rc = ozk ? oz::gemm<L>(true, L21, U12, A22, n2, n2, jb, oz_ws, oz_status, s, note_launch)
+      int rc = ozk ? oz::gemm<L>(true, L21, U12, A22, n2, n2, jb, oz_ws, oz_status, s, note_launch, Se)
                    : launch_gemm<L>(method, true, L21, U12, A22, SL, SU, n2, n2, jb, s);
       if (rc) return rc;
     }
@@ -597,9 +601,11 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
 
 template <int L>
 int gemm(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const double *Ap, int64_t lda, const double *Bp,
-         int64_t ldb, double *Cp, int64_t ldc, cudaStream_t s) {
+         int64_t ldb, double *Cp, int64_t ldc, cudaStream_t s, int ozaki_slices = 0) {
   if (beta_mode != 0 && beta_mode != 1) return -1;
   if (method != MCLU_METHOD_4M && method != MCLU_METHOD_3M && method != MCLU_METHOD_OZAKI) return -2;
+  // ozaki_slices: 0 (default) or 1 .. S, checked by the caller
+  const int Se = ozaki_slices ? ozaki_slices : oz::default_slices<L>();
   if (m < 0) return -3;
   if (n < 0) return -4;
   if (k < 0) return -5;
@@ -618,7 +624,7 @@ int gemm(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const doubl
     int *status = (int *)((char *)w.p + oz::ws_bytes<L>(m, n, k));
     MCLU_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
     ProfScope ps(PK_GEMM, s);
-    return oz::gemm<L>(beta_mode == 1, A, B, C, m, n, k, w.p, status, s, note_launch);
+    return oz::gemm<L>(beta_mode == 1, A, B, C, m, n, k, w.p, status, s, note_launch, Se);
   }
   if (method == MCLU_METHOD_3M && k > 0) {
     MCLU_TRY(w.alloc((size_t)(m * k + k * n) * L * sizeof(double) + 512, s));
@@ -715,6 +721,15 @@ int vec_op(int op, int64_t count, const double *x, const double *y, double *z, c
   extern "C" int zgemm_##SUF(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const double *A,       \
                              int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc, void *stream) { \
     return mclu::gemm<LIMBS>(beta_mode, method, m, n, k, A, lda, B, ldb, C, ldc, (cudaStream_t)stream);        \
+  }                                                                                                              \
+  extern "C" int zgemm_##SUF##_ex(int beta_mode, int method, int ozaki_slices, int64_t m, int64_t n, int64_t k,   \
+                                 const double *A, int64_t lda, const double *B, int64_t ldb, double *C,          \
+                                 int64_t ldc, void *stream) {                                                    \
+    if (ozaki_slices < 0) return -3;                                                                             \
+    if (ozaki_slices > mclu::oz::Cfg<LIMBS>::S) return MCLU_ERR_UNSUPPORTED;                                     \
+    int rc = mclu::gemm<LIMBS>(beta_mode, method, m, n, k, A, lda, B, ldb, C, ldc, (cudaStream_t)stream,        \
+                               ozaki_slices);                                                                    \
+    return rc <= -3 ? rc - 1 : rc; /* the arguments after ozaki_slices are one place further */                 \
   }                                                                                                              \
   extern "C" int zadjoint_rank1_##SUF(int64_t n, const double *lambda, const double *x, double *Abar,           \
                                       int64_t ldab, void *stream) {                                             \

@@ -86,4 +86,56 @@ extern "C" const char *mclu_status_string(int status) {
   return cudaGetErrorString((cudaError_t)status);
 }
 
-extern "C" const char *mclu_version(void) { return "0.1.0"; }
+extern "C" const char *mclu_version(void) { return "0.2.0"; }
+
+namespace {
+// FP64 throughput probe: every thread runs 8 independent DFMA chains, so the
+// FP64 units see no dependency stalls; 4 CTAs of 256 threads per SM.
+__global__ void k_fp64_probe(double *out, int iters, double mul, double add) {
+  double a[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) a[c] = 1.0 + 1e-3 * c + 1e-9 * threadIdx.x;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) a[c] = __fma_rn(a[c], mul, add);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; c++) s = __dadd_rn(s, a[c]);
+  if (s == -1.0) out[0] = s;  // never true: keeps the chains live
+}
+}  // namespace
+
+extern "C" int mclu_probe_fp64_rate(double *ops_per_second) {
+  if (ops_per_second == nullptr) return -1;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return (int)e;
+  double *d = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaMalloc(&d, sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int grid = 4 * sms, block = 256, iters = 40000;
+  if (e == cudaSuccess) {
+    k_fp64_probe<<<grid, block, 0, st>>>(d, iters / 8, 0.9999999, 1e-7);  // warm-up
+    e = cudaEventRecord(e0, st);
+  }
+  if (e == cudaSuccess) {
+    k_fp64_probe<<<grid, block, 0, st>>>(d, iters, 0.9999999, 1e-7);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) *ops_per_second = (double)grid * block * iters * 8.0 / (ms * 1e-3);
+  if (e1) cudaEventDestroy(e1);
+  if (e0) cudaEventDestroy(e0);
+  if (st) cudaStreamDestroy(st);
+  if (d) cudaFree(d);
+  return (int)e;
+}

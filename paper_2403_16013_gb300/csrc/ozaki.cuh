@@ -71,6 +71,13 @@ struct Cfg<4> {
   static constexpr int BETA = 7, S = 32, N = 16, FW = 9, TW = 8, RW = 10, GS = 6, EW = 8, EF = 0;
 };
 
+// Slices kept per operand when the caller asks for the default (ozaki_slices
+// = 0): the full S of the precision.
+template <int L>
+constexpr int default_slices() {
+  return Cfg<L>::S;
+}
+
 constexpr int KC = 64;         // realified K per chunk (32 complex columns of A)
 constexpr int NB_MAX = KC / 2; // complex panel width per chunk
 constexpr int BM = 128;        // tile rows (TMEM lanes)
@@ -312,7 +319,7 @@ __device__ __forceinline__ void digits_of(const double (&x)[L], int E, float (&d
 // A side: row i of the m x k block (k <= 32 per chunk), chunk c = blockIdx.y.
 // Output slices [chunk][S][Mpad][64] bf16: columns 0..31 hold Re, 32..63 Im.
 template <int L>
-__global__ void k_oz_split_a(View X, int64_t m, int64_t k, const int *Ea, __nv_bfloat16 *out, int64_t Mpad) {
+__global__ void k_oz_split_a(View X, int64_t m, int64_t k, const int *Ea, __nv_bfloat16 *out, int64_t Mpad, int Se) {
   constexpr int S = Cfg<L>::S;
   const int lane = threadIdx.x & 31;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -330,7 +337,8 @@ __global__ void k_oz_split_a(View X, int64_t m, int64_t k, const int *Ea, __nv_b
     digits_of<L>(x, E, dg);
     __nv_bfloat16 *o = out + (((int64_t)c * S) * Mpad + i) * KC + part * NB_MAX + lane;
 #pragma unroll
-    for (int p = 0; p < S; p++) o[(int64_t)p * Mpad * KC] = __float2bfloat16_rn(dg[p]);
+    for (int p = 0; p < S; p++)
+      if (p < Se) o[(int64_t)p * Mpad * KC] = __float2bfloat16_rn(dg[p]);
   }
 }
 
@@ -338,7 +346,7 @@ __global__ void k_oz_split_a(View X, int64_t m, int64_t k, const int *Ea, __nv_b
 // [chunk][S][Npad][64] with Npad >= 2n: row 2j = [Re B_.j ; -Im B_.j],
 // row 2j+1 = [Im B_.j ; Re B_.j] (K index: 0..31 first half, 32..63 second).
 template <int L>
-__global__ void k_oz_split_b(View X, int64_t k, int64_t n, const int *Eb, __nv_bfloat16 *out, int64_t Npad) {
+__global__ void k_oz_split_b(View X, int64_t k, int64_t n, const int *Eb, __nv_bfloat16 *out, int64_t Npad, int Se) {
   constexpr int S = Cfg<L>::S;
   const int lane = threadIdx.x & 31;
   const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -361,6 +369,7 @@ __global__ void k_oz_split_b(View X, int64_t k, int64_t n, const int *Eb, __nv_b
   __nv_bfloat16 *o1 = o0 + KC;
 #pragma unroll
   for (int q = 0; q < S; q++) {
+    if (q >= Se) break;
     const int64_t so = (int64_t)q * Npad * KC;
     o0[so + lane] = __float2bfloat16_rn(dre[q]);
     o0[so + NB_MAX + lane] = __float2bfloat16_rn(-dim[q]);
@@ -603,14 +612,14 @@ __device__ __forceinline__ void finish2(const uint32_t (&F)[FW], int eF, const d
 // broadcast so the warp stays converged for the .sync.aligned loads).
 template <int L, int NH, int D0>
 __device__ __forceinline__ bool fold_diagonals(uint32_t (&F)[NH][Cfg<L>::FW], uint32_t tbase, uint64_t *bar_grp,
-                                               uint32_t parity, int lane) {
+                                               uint32_t parity, int lane, int Se) {
   constexpr int S = Cfg<L>::S, N = Cfg<L>::N, BETA = Cfg<L>::BETA, FW = Cfg<L>::FW;
   constexpr int GS = Cfg<L>::GS;
   constexpr int G = (S - D0) < GS ? (S - D0) : GS;
+  if (D0 >= Se) return true;  // diagonals of dropped slice pairs: nothing was accumulated
   if (Cfg<L>::EF || D0 == 0) {
-    constexpr int NGRP = (S + GS - 1) / GS;
     int got = 0;
-    if (lane == 0) got = mbar_wait(&bar_grp[Cfg<L>::EF ? D0 / GS : NGRP - 1], parity) ? 1 : 0;
+    if (lane == 0) got = mbar_wait(&bar_grp[Cfg<L>::EF ? D0 / GS : (Se - 1) / GS], parity) ? 1 : 0;
     got = __shfl_sync(0xffffffffu, got, 0);
     if (!got) return false;
     __syncwarp();
@@ -622,15 +631,19 @@ __device__ __forceinline__ bool fold_diagonals(uint32_t (&F)[NH][Cfg<L>::FW], ui
 #pragma unroll
   for (int t = 0; t < G; t++) {
     uint32_t v[NH];
-    tmem_ld<NH>(tbase + (uint32_t)((D0 + t) * N), v);
-    tmem_wait_ld();
+#pragma unroll
+    for (int cc = 0; cc < NH; cc++) v[cc] = 0u;  // 0.0f: a diagonal past the last kept one
+    if (D0 + t < Se) {                          // warp-uniform
+      tmem_ld<NH>(tbase + (uint32_t)((D0 + t) * N), v);
+      tmem_wait_ld();
+    }
 #pragma unroll
     for (int cc = 0; cc < NH; cc++) g[cc] = g[cc] * (1LL << BETA) + (long long)__float2int_rz(__uint_as_float(v[cc]));
   }
 #pragma unroll
   for (int cc = 0; cc < NH; cc++) fold64<FW, BETA *(S - D0 - G)>(F[cc], g[cc]);
   if constexpr (D0 + G < S)
-    return fold_diagonals<L, NH, D0 + G>(F, tbase, bar_grp, parity, lane);
+    return fold_diagonals<L, NH, D0 + G>(F, tbase, bar_grp, parity, lane, Se);
   else
     return true;
 }
@@ -644,7 +657,7 @@ __device__ __forceinline__ bool fold_diagonals(uint32_t (&F)[NH][Cfg<L>::FW], ui
 template <int L, bool BETA>
 __global__ void __launch_bounds__(threads_of<L>(), 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, View C, int64_t m,
-              int64_t n, int nchunks, int Mpad, int Npad, const int *Ea, const int *Eb, int *status) {
+              int64_t n, int nchunks, int Mpad, int Npad, const int *Ea, const int *Eb, int *status, int Se) {
   using CF = Cfg<L>;
   constexpr int S = CF::S, N = CF::N, BETA_B = CF::BETA, FW = CF::FW, RW = CF::RW;
   constexpr int A_BYTES = BM * KC * 2;  // 16 KB
@@ -696,10 +709,10 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
             s_err = 1;
             break;
           }
-          mbar_expect_tx(&bar_bfull, B_BYTES);
-          for (int q = 0; q < S; q++)
+          mbar_expect_tx(&bar_bfull, (uint32_t)(Se * B_TILE));
+          for (int q = 0; q < Se; q++)
             tma_load_2d(sB + q * B_TILE, &tmB, &bar_bfull, 0, (c * S + q) * Npad + ntile * N);
-          for (int p = 0; p < S; p++, a_it++) {
+          for (int p = 0; p < Se; p++, a_it++) {
             const int st = a_it % NST;
             const uint32_t ph = (a_it / NST) & 1;
             if (!mbar_wait(&bar_aempty[st], ph ^ 1)) {
@@ -730,7 +743,7 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
             break;
           }
           tc_fence_after();
-          for (int p = 0; p < S; p++, a_it++) {
+          for (int p = 0; p < Se; p++, a_it++) {
             const int st = a_it % NST;
             if (!mbar_wait(&bar_afull[st], (a_it / NST) & 1)) {
               s_err = 4;
@@ -738,11 +751,12 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
             }
             tc_fence_after();
             const uint32_t a0 = smem_u32(sA + st * A_BYTES);
-            // The S B slices lie back to back in one K-major, 128-byte-swizzled
-            // layout (each a multiple of 1024 bytes), so A_p times slices
-            // 0 .. S-1-p is one product with (S - p) N columns, landing on the
-            // TMEM column blocks of diagonals p .. S-1 (split at 256 columns).
-            const int ncols = (S - p) * N;
+            // The Se kept B slices lie back to back in one K-major,
+            // 128-byte-swizzled layout (each a multiple of 1024 bytes), so A_p
+            // times slices 0 .. Se-1-p is one product with (Se - p) N columns,
+            // landing on the TMEM column blocks of diagonals p .. Se-1 (split
+            // at 256 columns).
+            const int ncols = (Se - p) * N;
             for (int c0 = 0; c0 < ncols; c0 += 256) {
               const int nn = min(256, ncols - c0);
               const uint32_t b0 = smem_u32(sB) + (uint32_t)(c0 * KC * 2);
@@ -755,7 +769,7 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
             umma_commit(&bar_aempty[st]);
             // diagonals of the group ending at p are complete: let the
             // epilogue fold them while the later slices multiply
-            if ((p + 1) % CF::GS == 0 || p == S - 1) umma_commit(&bar_grp[p / CF::GS]);
+            if ((p + 1) % CF::GS == 0 || p == Se - 1) umma_commit(&bar_grp[p / CF::GS]);
           }
           if (s_err) break;
           umma_commit(&bar_bempty);
@@ -780,7 +794,7 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
       for (int c = 0; c < nchunks; c++, r++) {
         // diagonal d sits in TMEM columns [d N, d N + N); each group is
         // folded as soon as its commit barrier completes
-        if (!fold_diagonals<L, NH, 0>(F, tbase, bar_grp, r & 1, lane)) {
+        if (!fold_diagonals<L, NH, 0>(F, tbase, bar_grp, r & 1, lane, Se)) {
           if (lane == 0) s_err = 5;
           ok = false;
           break;
@@ -894,7 +908,8 @@ inline int sm_count() {
 
 // Scales and slices of A (m x k, rows) and B (k x n, columns) into ws.
 template <int L>
-int split(View A, View B, int64_t m, int64_t n, int64_t k, void *ws, cudaStream_t s, void (*note)()) {
+int split(View A, View B, int64_t m, int64_t n, int64_t k, void *ws, cudaStream_t s, void (*note)(),
+          int Se = Cfg<L>::S) {
   const Sizes<L> z = sizes<L>(m, n, k);
   char *w = (char *)ws;
   __nv_bfloat16 *as = (__nv_bfloat16 *)w;
@@ -906,19 +921,21 @@ int split(View A, View B, int64_t m, int64_t n, int64_t k, void *ws, cudaStream_
   k_oz_scales<L><<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(B, n, k, false, Eb);
   note();
   k_oz_split_a<L><<<dim3((unsigned)((z.Mpad * 32 + 255) / 256), (unsigned)z.nchunks), 256, 0, s>>>(A, m, k, Ea, as,
-                                                                                                    z.Mpad);
+                                                                                                    z.Mpad, Se);
   note();
   k_oz_split_b<L><<<dim3((unsigned)((z.Npad / 2 * 32 + 255) / 256), (unsigned)z.nchunks), 256, 0, s>>>(
-      B, k, n, Eb, bs, z.Npad);
+      B, k, n, Eb, bs, z.Npad, Se);
   note();
   return (int)cudaGetLastError();
 }
 
 // C = C - A B (beta) or A B with the Ozaki scheme.  ws: ws_bytes<L>(m, n, k);
 // status: device int, OR-ed with a nonzero code if a pipeline wait timed out.
+// Se: slices kept per operand (1 .. S; pairs p + q <= Se - 1 are multiplied).
 template <int L>
 int gemm(bool beta, View A, View B, View C, int64_t m, int64_t n, int64_t k, void *ws, int *status, cudaStream_t s,
-         void (*note)()) {
+         void (*note)(), int Se = Cfg<L>::S) {
+  if (Se < 1 || Se > Cfg<L>::S) return (int)cudaErrorInvalidValue;
   if (m <= 0 || n <= 0) return 0;
   if (k == 0) {  // nothing to multiply (and nothing to split): C unchanged (beta) or zero
     if (!beta) {
@@ -930,7 +947,7 @@ int gemm(bool beta, View A, View B, View C, int64_t m, int64_t n, int64_t k, voi
     return 0;
   }
   const Sizes<L> z = sizes<L>(m, n, k);
-  int rc = split<L>(A, B, m, n, k, ws, s, note);
+  int rc = split<L>(A, B, m, n, k, ws, s, note, Se);
   if (rc) return rc;
   char *w = (char *)ws;
   int *Ea = (int *)(w + z.a_bytes + z.b_bytes);
@@ -951,12 +968,12 @@ int gemm(bool beta, View A, View B, View C, int64_t m, int64_t n, int64_t k, voi
     auto kern = k_oz_gemm<L, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
-    kern<<<grid, THREADS, smem, s>>>(tmA, tmB, C, m, n, (int)z.nchunks, (int)z.Mpad, (int)z.Npad, Ea, Eb, status);
+    kern<<<grid, THREADS, smem, s>>>(tmA, tmB, C, m, n, (int)z.nchunks, (int)z.Mpad, (int)z.Npad, Ea, Eb, status, Se);
   } else {
     auto kern = k_oz_gemm<L, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
-    kern<<<grid, THREADS, smem, s>>>(tmA, tmB, C, m, n, (int)z.nchunks, (int)z.Mpad, (int)z.Npad, Ea, Eb, status);
+    kern<<<grid, THREADS, smem, s>>>(tmA, tmB, C, m, n, (int)z.nchunks, (int)z.Mpad, (int)z.Npad, Ea, Eb, status, Se);
   }
   note();
   return (int)cudaGetLastError();

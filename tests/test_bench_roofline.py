@@ -61,10 +61,19 @@ def test_plain_update_ops_match_mac_count():
         assert r["ops_per_launch"] * launches == pytest.approx(macs * per * bench.I_REAL["td"])
 
 
+def _sha(name):
+    import hashlib
+    import os
+    with open(os.path.join(bench.ROOT, "paper_2403_16013_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
 def test_panel_traffic_only_for_the_captured_source(monkeypatch):
     n, steps = 4096, 1
     launches = n // 32
     prof = {"panel": (40.0, launches)}
+    # a capture taken on the current source is used ...
+    monkeypatch.setitem(bench.PANEL_TRAFFIC, "dd", dict(bench.PANEL_TRAFFIC["dd"], src_sha1=_sha("panel_coop.cuh")))
     r = bench.panel_roofline("ozaki", "dd", n, 128, steps, prof, el_ms=100.0)
     cap = bench.PANEL_TRAFFIC["dd"]
     rows = [n - s0 for s0 in range(0, n, 32)]
@@ -80,6 +89,7 @@ def test_panel_traffic_only_for_the_captured_source(monkeypatch):
 def test_trailing_traffic_only_for_the_captured_source(monkeypatch):
     n, nb, steps = 4096, 128, 1
     launches = n // nb - 1
+    monkeypatch.setitem(bench.OZ_TRAFFIC, "dd", dict(bench.OZ_TRAFFIC["dd"], src_sha1=_sha("ozaki.cuh")))
     r = bench.roofline("ozaki", "dd", n, nb, steps, {"gemm": (27.8, launches)}, el_ms=111.6)
     cap = bench.OZ_TRAFFIC["dd"]
     n2s = [n - j0 - nb for j0 in range(0, n - nb, nb)]

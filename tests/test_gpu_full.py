@@ -5,8 +5,16 @@ size and that the oracle can evaluate one output at a time:
 * backward error with the exact residual: ||b - A x|| / (||A|| ||x||) <= 16 n u;
 * sampled entries of L U equal those of P A within 2^6 n u max|A|
   (each entry is an exact dot product evaluated by the oracle);
-* partial pivoting on cabs1 bounds every multiplier: |l_ik| <= sqrt(2).
+* partial pivoting on cabs1 bounds every multiplier: |l_ik| <= sqrt(2);
+* against the oracle's own run on the same matrix (fixtures under
+  tests/golden written by make_full_pivots.py from the oracle alone: DD and TD
+  at n = 4096, QD at n = 2048): the pivot sequence identical (bit-exact
+  integers), 64 sampled entries of the factors within 2^10 n u max|A| max|LU|
+  and 64 sampled solution entries within 2^12 n u max|x| of the oracle's.
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
@@ -15,6 +23,12 @@ from helpers import U_EXP
 from paper_2403_16013_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+sys.path.insert(0, GOLDEN)
+import make_golden  # noqa: E402
+
+# (precision, order) of the oracle fixtures
+FIXTURES = {("dd", 4096), ("td", 4096), ("qd", 2048)}
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +51,7 @@ def _apply_pivots(A, ipiv):
 
 @pytest.mark.parametrize("prec,method,n", [("dd", "4m", 4096), ("dd", "3m", 4096), ("td", "4m", 4096),
                                            ("qd", "4m", 4096), ("dd", "ozaki", 4096), ("td", "ozaki", 4096),
-                                           ("qd", "ozaki", 4096),
+                                           ("qd", "ozaki", 4096), ("qd", "4m", 2048), ("qd", "ozaki", 2048),
                                            # more than 32 panel rows per CTA (152 CTAs) in the first panels
                                            ("dd", "ozaki", 5120), ("td", "ozaki", 5120)])
 def test_full_size(api, orc, prec, method, n):
@@ -68,3 +82,15 @@ def test_full_size(api, orc, prec, method, n):
     amax = np.abs(A[:, 0]).max()
     err = np.abs(d[:, :, 0]).max()
     assert err <= 2.0 ** 6 * n * 2.0 ** -U_EXP[L] * amax, err
+    if (prec, n) in FIXTURES:
+        g = make_golden.load(os.path.join(GOLDEN, f"full_{prec}_n{n}.txt"))
+        assert int(g["n"][0]) == n and int(g["info"][0]) == 0
+        mism = np.nonzero(ip != g["ipiv"])[0]
+        assert mism.size == 0, ("pivots differ from the oracle", mism[:4], ip[mism[:4]], g["ipiv"][mism[:4]])
+        u = 2.0 ** -U_EXP[L]
+        lu = LUh[:, :, g["lu_cols"], g["lu_rows"]].transpose(2, 0, 1)          # [s, 2, L]
+        dl = np.abs((lu - g["lu"]).sum(axis=2)).max()
+        assert dl <= 2.0 ** 10 * n * u * amax * max(1.0, np.abs(g["lu"][:, :, 0]).max()), dl
+        xg = X[:, :, 0, g["x_rows"]].transpose(2, 0, 1)
+        dx = np.abs((xg - g["x"]).sum(axis=2)).max()
+        assert dx <= 2.0 ** 12 * n * u * np.abs(g["x"][:, :, 0]).max(), dx

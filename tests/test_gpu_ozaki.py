@@ -174,3 +174,52 @@ def test_lu_ozaki_known_factor_bit_exact(api, L, nb):
     LU, ipiv, info = api.lu_factor(dev(A), method="ozaki", nb=nb)
     assert np.array_equal(host(ipiv), ipiv_ref)
     assert np.array_equal(host(LU), packed)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+@pytest.mark.parametrize("frac", [0.5, 1.0])
+def test_zgemm_ozaki_fewer_slices(api, orc, L, frac):
+    """Se < S slices per operand (the accuracy knob of Sec. 2.3: the number
+    of divisions): against the exact product within the Ozaki bound with Se
+    in place of S, 2^(Ea_i + Eb_j - beta Se) 2k (L + Se + 2) + 2^(2 - 53L)|result|;
+    Se = S - 1 and about S / 2."""
+    beta, S = ozaki.CFG[L]
+    Se = S - 1 if frac == 1.0 else S // 2
+    m, n, k = 150, 45, 70
+    A = inputs.spread_matrix(m, k, L, seed=51, spread=12)
+    B = inputs.spread_matrix(k, n, L, seed=52, spread=12)
+    C0 = inputs.gaussian_matrix(n, L, seed=53, rows=m)
+    out = host(api.zgemm(dev(A), dev(B), dev(C0), method="ozaki", ozaki_slices=Se))
+    rows, cols = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    rows, cols = rows.ravel(), cols.ravel()
+    ex = orc.exact_entries(A, B, rows, cols, C=C0, sign=-1)
+    Ea, _ = ozaki.split_rows(A, m, k, L)
+    Eb, _ = ozaki.split_cols(B, k, n, L)
+    g = np.stack([out[0, :, cols, rows], out[1, :, cols, rows]], axis=1)
+    V = np.concatenate([g, -ex], axis=2).reshape(-1, L + 4)
+    d = np.abs(orc.exact_sum_rows(V, 1)[:, 0].reshape(-1, 2))
+    scale = np.ldexp(1.0, (Ea[rows] + Eb[cols] - beta * Se).astype(int)) * 2 * k * (L + Se + 2)
+    tol = scale[:, None] + 2.0 ** (2 - 53 * L) * np.abs(ex[:, :, 0])
+    assert np.all(d <= tol), float(np.max(d / tol))
+    if frac == 0.5:   # far fewer bits than the precision: the error must show (the knob acts)
+        full = host(api.zgemm(dev(A), dev(B), dev(C0), method="ozaki"))
+        assert not np.array_equal(full, out)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_lu_ozaki_one_slice_fewer(api, orc, L):
+    """The LU with Se = S - 1 (every Ozaki product of the factorisation):
+    the oracle's pivots, backward error within 16 n u 2^(beta (S - Se))."""
+    beta, S = ozaki.CFG[L]
+    n = 200 if L < 4 else 150
+    A = inputs.gaussian_matrix(n, L, seed=1)
+    LU, ipiv, info = api.lu_factor(dev(A), method="ozaki", ozaki_slices=S - 1)
+    assert int(host(info)[0]) == 0
+    LUo, ipo, _, gap = orc.zgetrf(A)
+    ipg = host(ipiv)
+    mism = np.nonzero(ipg != ipo)[0]
+    assert mism.size == 0, ("pivots differ", mism[:4], ipg[mism[:4]], ipo[mism[:4]], gap[mism[:4]])
+    xr, xi = inputs.ones_x_true(n)
+    b = inputs.truncate_limbs(inputs.exact_rhs(A, xr, xi, L_out=4), L)
+    x = host(api.lu_solve(LU, ipiv, dev(b)))
+    assert backward_error(orc, A, x, b) <= bound(n, L) * 2.0 ** beta
