@@ -106,6 +106,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle sample")
     p.add_argument("--slices", type=int, default=0, help="Ozaki slices per operand (0: the precision's default)")
+    p.add_argument("--sub-nb", type=int, default=0, help="Ozaki sub-panel width (0: the library's default)")
     p.add_argument("--no-precisions", action="store_true", help="skip the TD / QD steps of the default line")
     p.add_argument("--no-zgemm", action="store_true", help="skip the 1024^3 ZGEMM sub-object of the default line")
     p.add_argument("--slices-sweep", action="store_true",
@@ -263,7 +264,7 @@ def run_reference(args):
 
 
 def panel_roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: dict, el_ms: float,
-                   fp64: float | None = None):
+                   fp64: float | None = None, sub_nb: int = 0):
     """Roofline of the cooperative panel kernel (FP64 pipe): the algorithmic
     FP64 operations of its multipliers and rank-1 updates (4 real
     product-accumulates of I_REAL operations per complex multiply-accumulate)
@@ -271,7 +272,7 @@ def panel_roofline(method: str, prec: str, n: int, nb: int, steps: int, prof: di
     panel_ms, panel_calls = prof["panel"]
     if not panel_calls:
         return None
-    w = 32 if method == "ozaki" else nb  # panel width of one launch
+    w = (sub_nb or 32) if method == "ozaki" else nb  # panel width of one launch
     macs = 0
     for s0 in range(0, n, w):
         ww = min(w, n - s0)
@@ -422,17 +423,19 @@ def run_sweep(args):
                           "info": int(info.item())}), flush=True)
 
 
-def lu_step_fn(api, A, A0, x, b0, ipiv, info, method, nb, slices):
+def lu_step_fn(api, A, A0, x, b0, ipiv, info, method, nb, slices, sub_nb=0):
     def step():
         A.copy_(A0)
-        api.lu_factor_(A, ipiv, info, method=method, nb=nb, ozaki_slices=slices if method == "ozaki" else 0)
+        oz = method == "ozaki"
+        api.lu_factor_(A, ipiv, info, method=method, nb=nb, ozaki_slices=slices if oz else 0,
+                       sub_nb=sub_nb if oz else 0)
         x.copy_(b0)
         api.lu_solve(A, ipiv, x, inplace=True)
     return step
 
 
 def time_lu(ctx, prec, method, nb, steps, warmup, slices=0, sampler=None, ws=1, stream=None, fp64=None,
-            warm_n=0):
+            warm_n=0, sub_nb=0):
     """LU + solve of the prec's benchmark matrix: warm-up steps (at order warm_n
     when given, which loads the kernels without the cost of full-size steps),
     then `steps` steps between barriers and CUDA events on the library's stream,
@@ -444,13 +447,13 @@ def time_lu(ctx, prec, method, nb, steps, warmup, slices=0, sampler=None, ws=1, 
     A, x = torch.empty_like(A0), torch.empty_like(b0)
     ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
-    step = lu_step_fn(api, A, A0, x, b0, ipiv, info, method, nb, slices)
+    step = lu_step_fn(api, A, A0, x, b0, ipiv, info, method, nb, slices, sub_nb)
     if warm_n:
         Aw = A0[:, :, :warm_n, :warm_n].contiguous()
         bw = b0[:, :, :, :warm_n].contiguous()
         Ax, xw = torch.empty_like(Aw), torch.empty_like(bw)
         ipw = torch.empty(warm_n, dtype=torch.int32, device="cuda")
-        wstep = lu_step_fn(api, Ax, Aw, xw, bw, ipw, info, method, nb, slices)
+        wstep = lu_step_fn(api, Ax, Aw, xw, bw, ipw, info, method, nb, slices, sub_nb)
         for _ in range(max(1, warmup)):
             wstep()
     else:
@@ -480,7 +483,7 @@ def time_lu(ctx, prec, method, nb, steps, warmup, slices=0, sampler=None, ws=1, 
     if int(info.item()) != 0:
         raise RuntimeError(f"zgetrf info {int(info.item())} on the benchmark matrix")
     upd = roofline(method, prec, n, nb, steps, prof, el_ms, fp64=fp64, slices=slices)
-    pan = panel_roofline(method, prec, n, nb, steps, prof, el_ms, fp64=fp64)
+    pan = panel_roofline(method, prec, n, nb, steps, prof, el_ms, fp64=fp64, sub_nb=sub_nb)
     # the "roofline" object describes the kernel with the largest share of the step
     first, second = (pan, upd) if (pan and (not upd or pan["share_of_step"] > upd["share_of_step"])) else (upd, pan)
     eta = backward_error(api, A0, x, b0)
@@ -635,7 +638,7 @@ def main():
     stream = torch.cuda.current_stream()
     method, nb = args.method, nb_of(args.method)
     main_run = time_lu(ctx, prec, method, nb, args.steps, args.warmup, slices=args.slices,
-                       sampler=ClockSampler(local), ws=ws, stream=stream, fp64=fp64)
+                       sampler=ClockSampler(local), ws=ws, stream=stream, fp64=fp64, sub_nb=args.sub_nb)
     bound = 16.0 * n * 2.0 ** -U_EXP[prec]
     A_bytes = ctx["inputs"][prec][0].numel() * 8
     line = {"metric": "complex DD/TD/QD LU GFLOPS (8n^3/3/t) at n=4096", "value": main_run["value"],

@@ -57,7 +57,9 @@ typedef struct mclu_opts {
   int32_t method;       /* MCLU_METHOD_*; default MCLU_METHOD_4M                             */
   int32_t ozaki_slices; /* MCLU_METHOD_OZAKI: slices kept per operand, 1..S (S = 14 DD, 24 TD, */
                         /*   32 QD; above S: MCLU_ERR_UNSUPPORTED); 0 = the precision's S     */
-  int32_t reserved;     /* must be 0                                                          */
+  int32_t sub_nb;       /* MCLU_METHOD_OZAKI: width of the sub-panels each block is factored  */
+                        /*   in (the columns between them updated by Ozaki products), 1..32; */
+                        /*   0 = 32.  Must be 0 for the other methods                         */
 } mclu_opts;
 
 /*
@@ -207,12 +209,7 @@ int zozaki_split_qd(int side, int64_t rows, int64_t cols, const double *X, int64
  *          complex ops on plane arrays [2][L][count]:
  *            10 add, 11 sub, 12 mul (4M, Eq. 1), 13 mul (3M, Eq. 2),
  *            14 div, 15 inv (reciprocal), 16 cabs1 (result in the real part)
- *          the integer-pipe forms used by the panel factorisation (exact
- *          sums of limbs and limb products, rounded to L limbs):
- *            20 mul (Eq. 1), 21 z - x y (z is read, then overwritten),
- *            22 cabs1 (result in the real part), 23 inv (Newton steps on
- *            the integer frame from a binary64 start)
- *   x, y   device inputs (y ignored by 15, 16, 22, 23); z device output
+ *   x, y   device inputs (y ignored by 15, 16); z device output
  */
 int mclu_vec_op(int op, int L, int64_t count, const double *x, const double *y, double *z, void *stream);
 

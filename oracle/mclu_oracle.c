@@ -59,8 +59,10 @@
 
 static int g_err = 0; /* sticky: a normalisation did not reach its fixed point or a buffer overflowed */
 
-int orc_error_flag(void) { return g_err; }
-void orc_clear_error(void) { g_err = 0; }
+/* g_err is set from OpenMP threads: every access is atomic */
+static void set_err(int bit) { __atomic_fetch_or(&g_err, bit, __ATOMIC_RELAXED); }
+int orc_error_flag(void) { return __atomic_load_n(&g_err, __ATOMIC_RELAXED); }
+void orc_clear_error(void) { __atomic_store_n(&g_err, 0, __ATOMIC_RELAXED); }
 int orc_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
@@ -131,7 +133,7 @@ static int normalize(double *v, int m) {
     m = k;
     if (!changed) return m;
   }
-  g_err |= 1;
+  set_err(1);
   return m;
 }
 
@@ -196,7 +198,7 @@ static void mc_div(int L, const double *a, const double *b, double *z) {
     if (mr == 0) break;
     double qk = r[0] / bn[0];
     q[nq++] = qk;
-    if (mr + 2 * mb > MAXT) { g_err |= 2; break; }
+    if (mr + 2 * mb > MAXT) { set_err(2); break; }
     for (int j = 0; j < mb; j++) {
       double p, e;
       two_prod(qk, bn[j], &p, &e);
@@ -502,7 +504,7 @@ int orc_zgetrf(int L, int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t 
   }
   free(keys);
   free(klen);
-  return g_err ? 1 : 0;
+  return orc_error_flag() ? 1 : 0;
 }
 
 /*
@@ -592,7 +594,7 @@ int orc_zgetrs(int L, char trans, int64_t n, int64_t nrhs, const double *A, int6
       }
     }
   }
-  return g_err ? 1 : 0;
+  return orc_error_flag() ? 1 : 0;
 }
 
 /*
@@ -643,7 +645,7 @@ int orc_zgemm(int L, int method, int beta_mode, int64_t m, int64_t n, int64_t k,
       st_elem(L, C, ldc, n, i, j, &acc);
     }
   }
-  return g_err ? 1 : 0;
+  return orc_error_flag() ? 1 : 0;
 }
 
 /* ------------------------------------------------- superaccumulator -- */
@@ -880,7 +882,7 @@ int orc_adjoint(int L, int64_t n, const double *LU, int64_t lda, const int32_t *
       st_elem(L, Abar, ldab, n, i, j, &t);
     }
   }
-  return g_err ? 1 : 0;
+  return orc_error_flag() ? 1 : 0;
 }
 
 /*
@@ -948,7 +950,7 @@ int orc_make_ill_conditioned(int L, int64_t n, int h, const double *V1, const do
   }
   for (int j = h - 1; j >= 0; j--) apply_reflector(L, n, A, V2 + (size_t)j * 2 * n, 0);
   for (int j = h - 1; j >= 0; j--) apply_reflector(L, n, A, V1 + (size_t)j * 2 * n, 1);
-  return g_err ? 1 : 0;
+  return orc_error_flag() ? 1 : 0;
 }
 
 /* ------------------------------------------------ real LU and solve -- */
@@ -1056,7 +1058,7 @@ int orc_dgetrf(int L, int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t 
   }
   free(keys);
   free(klen);
-  return g_err ? 1 : 0;
+  return orc_error_flag() ? 1 : 0;
 }
 
 /*
@@ -1144,5 +1146,5 @@ int orc_dgetrs(int L, char trans, int64_t n, int64_t nrhs, const double *A, int6
       }
     }
   }
-  return g_err ? 1 : 0;
+  return orc_error_flag() ? 1 : 0;
 }

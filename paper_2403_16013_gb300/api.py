@@ -35,25 +35,27 @@ def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
 
 
-def lu_factor(A: torch.Tensor, method: str = "4m", nb: int = 0, ozaki_slices: int = 0, out: torch.Tensor | None = None):
-    """P A = L U.  Returns (LU planes, ipiv int32 1-based, info int32[1] device)."""
+def lu_factor(A: torch.Tensor, method: str = "4m", nb: int = 0, ozaki_slices: int = 0, out: torch.Tensor | None = None,
+              sub_nb: int = 0):
+    """P A = L U.  Returns (LU planes, ipiv int32 1-based, info int32[1] device).
+    ozaki_slices, sub_nb: the Ozaki method's slices per operand and sub-panel width (0: defaults)."""
     _check_planes(A, "A")
     n, lda = A.shape[2], A.shape[3]
     LU = A.clone() if out is None else out.copy_(A)
     ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
     info = torch.zeros(1, dtype=torch.int32, device=A.device)
     rc = B.zgetrf_ex(_prec(A), n, LU.data_ptr(), lda, ipiv.data_ptr(), info.data_ptr(), nb, METHODS[method],
-                     ozaki_slices, _stream())
+                     ozaki_slices, _stream(), sub_nb=sub_nb)
     B.check(rc, "zgetrf")
     return LU, ipiv[:n], info
 
 
 def lu_factor_(A: torch.Tensor, ipiv: torch.Tensor, info: torch.Tensor | None = None, method: str = "4m",
-               nb: int = 0, ozaki_slices: int = 0):
+               nb: int = 0, ozaki_slices: int = 0, sub_nb: int = 0):
     """In-place factorisation into caller-owned buffers (no allocation besides the library's workspace)."""
     n, lda = A.shape[2], A.shape[3]
     rc = B.zgetrf_ex(_prec(A), n, A.data_ptr(), lda, ipiv.data_ptr(), 0 if info is None else info.data_ptr(), nb,
-                     METHODS[method], ozaki_slices, _stream())
+                     METHODS[method], ozaki_slices, _stream(), sub_nb=sub_nb)
     B.check(rc, "zgetrf")
 
 
@@ -95,16 +97,15 @@ def adjoint_rank1(lam: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
 
 
 _VEC_OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "cadd": 10, "csub": 11, "cmul": 12, "cmul3m": 13,
-            "cdiv": 14, "cinv": 15, "cabs1": 16, "icmul": 20, "icfms": 21, "icabs1": 22, "icinv": 23}
+            "cdiv": 14, "cinv": 15, "cabs1": 16}
 
 
 def vec_op(op: str, x: torch.Tensor, y: torch.Tensor | None = None, z: torch.Tensor | None = None) -> torch.Tensor:
-    """Elementwise MC arithmetic: real ops on [L, count], complex ops on [2, L, count].
-    "icfms" computes z - x y (z is the third operand); the other ops ignore z."""
+    """Elementwise MC arithmetic: real ops on [L, count], complex ops on [2, L, count]."""
     code = _VEC_OPS[op]
     L = x.shape[0] if code < 10 else x.shape[1]
     count = x.shape[-1]
-    z = z.clone() if (code == 21 and z is not None) else torch.empty_like(x)
+    z = torch.empty_like(x)
     rc = B.vec_op(code, L, count, x.data_ptr(), 0 if y is None else y.data_ptr(), z.data_ptr(), _stream())
     B.check(rc, f"vec_op {op}")
     return z

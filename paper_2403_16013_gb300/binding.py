@@ -19,7 +19,7 @@ LIMBS = {"dd": 2, "td": 3, "qd": 4}
 
 
 class MCLUOpts(C.Structure):
-    _fields_ = [("nb", C.c_int32), ("method", C.c_int32), ("ozaki_slices", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("nb", C.c_int32), ("method", C.c_int32), ("ozaki_slices", C.c_int32), ("sub_nb", C.c_int32)]
 
 
 _lib = None
@@ -125,8 +125,9 @@ def zgetrf(prec: str, n, A, lda, ipiv, stream=None) -> int:
     return getattr(load(), f"zgetrf_{prec}")(n, A, lda, ipiv, _stream(stream))
 
 
-def zgetrf_ex(prec: str, n, A, lda, ipiv, info, nb=0, method=METHOD_4M, ozaki_slices=0, stream=None) -> int:
-    o = MCLUOpts(nb, method, ozaki_slices, 0)
+def zgetrf_ex(prec: str, n, A, lda, ipiv, info, nb=0, method=METHOD_4M, ozaki_slices=0, stream=None,
+              sub_nb=0) -> int:
+    o = MCLUOpts(nb, method, ozaki_slices, sub_nb)
     return getattr(load(), f"zgetrf_{prec}_ex")(n, A, lda, ipiv, info, C.byref(o), _stream(stream))
 
 

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "../../include/mclu.h"
@@ -32,6 +33,22 @@ void note_launch();
   } while (0)
 
 constexpr int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per device:
+// the limit is a property of the function on one device, so bit d of `done`
+// records device d (devices 64 and up set it on every call).  Concurrent
+// first calls from several host threads may both set it (harmless).
+template <class K>
+inline cudaError_t smem_limit_once(K kern, int bytes, std::atomic<unsigned long long> &done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ULL << dev) : 0ULL;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 // Launch classes timed by mclu_profile_begin / mclu_profile_end.
 enum ProfKind { PK_PANEL = 0, PK_LASWP = 1, PK_TRSM = 2, PK_GEMM = 3, PK_SOLVE = 4, PK_OTHER = 5, PK_COUNT = 6 };
@@ -120,12 +137,8 @@ int launch_tri_block(dim3 grid, dim3 block, cudaStream_t s, View A, int64_t k0, 
                      const double *rdiag, int64_t rld, int64_t xrow0) {
   const size_t staged = tri_block_smem<L>(bs, (int)block.y, true);
   if (staged <= 200 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      MCLU_TRY(cudaFuncSetAttribute(k_tri_block<L, LOWER, UNIT, CONJT, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    MCLU_TRY(smem_limit_once(k_tri_block<L, LOWER, UNIT, CONJT, true>, 200 * 1024, attr));
     k_tri_block<L, LOWER, UNIT, CONJT, true><<<grid, block, staged, s>>>(A, k0, bs, X, ncols, rdiag, rld, xrow0);
   } else {
     k_tri_block<L, LOWER, UNIT, CONJT, false>
@@ -162,10 +175,9 @@ int launch_lsolve(cudaStream_t s, View A, int64_t k0, int bs, View X, int64_t nc
 template <int L>
 int launch_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int32_t *ipiv, PanelWS<L> ws, CoopWS cw,
                       cudaStream_t s) {
-  static int sms = 0, per_sm = -1;
   const int nb = (int)(jend - j0);
   const int64_t m = n - j0;
-  if (sms == 0) sms = oz::sm_count();
+  const int sms = oz::sm_count();
   if (nb > COOP_NB_MAX) return 1;
   int G = (int)std::min<int64_t>({(int64_t)sms, cdiv(m, 8), (int64_t)COOP_GMAX});
   if (G < 1) G = 1;
@@ -174,10 +186,8 @@ int launch_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int32_t *ipiv
   const size_t smem = (((size_t)rpc + 2) * nb * 2 * L + (size_t)4 * rpc * L) * sizeof(double);
   if (smem > 200 * 1024) return 1;
   auto kern = L == 2 ? k_panel_coop<L> : k_panel_team<L>;
-  if (per_sm < 0) {
-    MCLU_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    per_sm = 0;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  MCLU_TRY(smem_limit_once(kern, 200 * 1024, attr));
   int occ = 0;
   MCLU_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, COOP_T, smem));
   if ((int64_t)occ * sms < G) return 1;
@@ -232,12 +242,15 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   if (n > 0 && ipiv == nullptr) return -4;
   int nb = 64, method = MCLU_METHOD_4M;
   int Se = 0;  // Ozaki slices per operand (0: the precision's default)
+  int sbw = oz::NB_MAX;  // Ozaki: sub-panel width
   if (opts) {
     if (opts->nb < 0 || opts->nb > 256) return -6;
     if (opts->nb) nb = opts->nb;
     if (opts->method < MCLU_METHOD_4M || opts->method > MCLU_METHOD_OZAKI) return -6;
     method = opts->method;
-    if (opts->reserved != 0) return -6;
+    if (opts->sub_nb < 0 || opts->sub_nb > oz::NB_MAX) return -6;
+    if (opts->sub_nb != 0 && method != MCLU_METHOD_OZAKI) return -6;
+    if (opts->sub_nb) sbw = opts->sub_nb;
     if (method == MCLU_METHOD_OZAKI) {
       if (opts->ozaki_slices < 0) return -6;
       if (opts->ozaki_slices > oz::Cfg<L>::S) return MCLU_ERR_UNSUPPORTED;
@@ -323,12 +336,8 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     ProfScope ps(PK_LASWP, s);
     const size_t lsm = laswp_smem((int)(k1 - k0));
     if (lsm > 48 * 1024) {
-      static bool attr = false;
-      if (!attr) {
-        MCLU_TRY(cudaFuncSetAttribute(k_laswp_gather<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)laswp_smem(COOP_NB_MAX)));
-        attr = true;
-      }
+      static std::atomic<unsigned long long> attr{0};
+      MCLU_TRY(smem_limit_once(k_laswp_gather<L>, (int)laswp_smem(COOP_NB_MAX), attr));
     }
     k_laswp_gather<L><<<(unsigned)cdiv(ncols, LASWP_C), 256, lsm, s>>>(A, k0, k1, ipiv, c0, c1, x0, x1);
     MCLU_LAUNCHED();
@@ -341,13 +350,13 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
       int rc = panel(j0, jend);
       if (rc) return rc;
     } else {
-      // Ozaki: the block is factored as sub-panels of oz::NB_MAX columns, each
+      // Ozaki: the block is factored as sub-panels of sbw <= 32 columns, each
       // followed by the update of the block's remaining columns (their swaps,
       // their U rows by the block solve, an Ozaki product for the rest), so
       // that the trailing update below takes all jb columns in one product
       // (K = 2 jb realified: several TMEM chunks, one exact C - P per element).
-      for (int64_t s0 = j0; s0 < jend; s0 += oz::NB_MAX) {
-        const int64_t send = std::min<int64_t>(s0 + oz::NB_MAX, jend), sb = send - s0;
+      for (int64_t s0 = j0; s0 < jend; s0 += sbw) {
+        const int64_t send = std::min<int64_t>(s0 + sbw, jend), sb = send - s0;
         int rc = panel(s0, send);
         if (rc) return rc;
         rc = laswp(s0, send, j0, jend, s0, send);  // the block's other columns, in one launch
@@ -456,12 +465,8 @@ int tri_solve(View A, int64_t n, const double *W, View R, View Y, int64_t nrhs, 
   constexpr int BS = SOLVE_BS;
   constexpr size_t smem = blk_solve_smem<L>();
   if (smem > 48 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      MCLU_TRY(cudaFuncSetAttribute(k_blk_solve<L, LOWER, CONJT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    MCLU_TRY(smem_limit_once(k_blk_solve<L, LOWER, CONJT>, (int)smem, attr));
   }
   const int64_t nblk = cdiv(n, BS);
   for (int64_t c0 = 0; c0 < nrhs; c0 += 65535) {
@@ -487,20 +492,15 @@ int tri_solve(View A, int64_t n, const double *W, View R, View Y, int64_t nrhs, 
 template <int L, bool LOWER, bool CONJT>
 int tri_solve_flow(View A, int64_t n, const double *W, View R, View Y, int64_t nrhs, int *flags, int flagbase,
                    int *status, cudaStream_t s) {
-  static int sms = 0;
-  if (sms == 0) sms = oz::sm_count();
+  const int sms = oz::sm_count();
   const int64_t nblk = cdiv(n, SOLVE_BS);
   const int G = (int)std::min<int64_t>(sms, nblk);
   const int nown = (int)cdiv(nblk, G);
   const size_t smem = trsv_flow_smem<L>(nown);
   if (smem > 200 * 1024) return 1;
   if (smem > 48 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      MCLU_TRY(cudaFuncSetAttribute(k_trsv_flow<L, LOWER, CONJT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    200 * 1024));
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    MCLU_TRY(smem_limit_once(k_trsv_flow<L, LOWER, CONJT>, 200 * 1024, attr));
   }
   int occ = 0;
   MCLU_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trsv_flow<L, LOWER, CONJT>, FLOW_T, smem));
@@ -691,12 +691,12 @@ int ozaki_split(int side, int64_t rows, int64_t cols, const double *X, int64_t l
 template <int L>
 int vec_op(int op, int64_t count, const double *x, const double *y, double *z, cudaStream_t s) {
   const bool real = op >= 0 && op <= 3;
-  const bool cplx = (op >= 10 && op <= 16) || (op >= 20 && op <= 23);
+  const bool cplx = op >= 10 && op <= 16;
   if (!real && !cplx) return -1;
   if (count < 0) return -3;
   if (count == 0) return 0;
   if (!x) return -4;
-  if (!y && op != 15 && op != 16 && op != 22 && op != 23) return -5;
+  if (!y && op != 15 && op != 16) return -5;
   if (!z) return -6;
   k_vec_op<L><<<(unsigned)cdiv(count, 128), 128, 0, s>>>(op, count, x, y, z);
   MCLU_LAUNCHED();

@@ -19,7 +19,6 @@
 #include <climits>
 
 #include "mc.cuh"
-#include "mi.cuh"
 
 namespace mclu {
 
@@ -1448,22 +1447,7 @@ __global__ void k_vec_op(int op, int64_t count, const double *x, const double *y
   View vy{const_cast<double *>(y), count, count};
   View vz{z, count, count};
   Z<L> a = ldz<L>(vx, e, 0), b, r;
-  if (op != 15 && op != 16 && op != 22 && op != 23) b = ldz<L>(vy, e, 0);
-  if (op >= 20) {  // the integer-pipe forms
-    const mi::ZL<L> ua = mi::unpack<L>(a);
-    if (op == 20) {
-      r = mi::zi_mul<L>(ua, mi::unpack<L>(b));
-    } else if (op == 21) {
-      r = mi::zi_fms<L>(ldz<L>(vz, e, 0), ua, mi::unpack<L>(b));
-    } else if (op == 23) {
-      r = mi::zi_inv<L>(ua);
-    } else {
-      r.re = mi::zi_abs1<L>(ua);
-      r.im = r_zero<L>();
-    }
-    stz<L>(vz, e, 0, r);
-    return;
-  }
+  if (op != 15 && op != 16) b = ldz<L>(vy, e, 0);
   switch (op) {
     case 10: r = z_add<L>(a, b); break;
     case 11: r = z_sub<L>(a, b); break;

@@ -4,10 +4,15 @@ and 3M (Eq. 3), DD / TD / QD.
 
 * Against the exact product (the oracle's superaccumulator, every entry of
   ragged small shapes and 64 sampled entries of m = n = k = 1024): the 4M
-  result within 4 (k + 2) u_L sum|a||b| per component plus the rounding of
-  the result to L limbs, u_L = 2^-53L; the 3M imaginary part within Higham's
-  3M form 8 (k + 4) u_L (|Re a| + |Im a|)(|Re b| + |Im b|).  Both bounds are
-  the ones the oracle's own ZGEMM is pinned to.
+  result within 2 L^2 (k + 2) u_L sum|a||b| per component plus the rounding
+  of the result to L limbs, u_L = 2^-53L; the 3M imaginary part within
+  Higham's 3M form 2 (L^2 + 4) (k + 4) u_L (|Re a| + |Im a|)(|Re b| + |Im b|).
+  The GPU accumulates every real product in L levels, exactly (TwoSum,
+  TwoProd) down to the last level, where L^2 terms of order u^(L-1) |ab| per
+  product are added with rounding (4 / 9 / 16 for DD / TD / QD); each such
+  rounding costs at most 2^-53 times the last level's magnitude, about u^(L-1)
+  sum|ab|, hence the L^2 (k + 2) form (the oracle, which rounds the exact
+  result of every operation once, is pinned to the tighter 4 (k + 2)).
 * Dyadic operands whose every product and sum is exact in binary64: the GPU
   result equals the exact one bit for bit (catches any index, sign or
   transposition error exactly).
@@ -52,8 +57,9 @@ def _check_against_exact(orc, A, B, C, out, rows, cols, method):
     ri = (aR * bI + aI * bR).sum(axis=0)
     s3 = ((aR + aI) * (bR + bI)).sum(axis=0)
     rnd = 2.0 ** (2 - 53 * L) * np.abs(ex[:, :, 0])
-    tol_re = 4 * (k + 2) * u * rr * 1.01 + rnd[:, 0]
-    tol_im = (8 * (k + 4) * u * s3 if method == "3m" else 4 * (k + 2) * u * ri) * 1.01 + rnd[:, 1]
+    c4, c3 = 2 * L * L, 2 * (L * L + 4)
+    tol_re = c4 * (k + 2) * u * rr * 1.01 + rnd[:, 0]
+    tol_im = (c3 * (k + 4) * u * s3 if method == "3m" else c4 * (k + 2) * u * ri) * 1.01 + rnd[:, 1]
     if C is not None:   # the subtraction from C adds one rounding of |C| at the last level
         cabs = np.abs(C[:, 0][:, cols, rows])                                            # [2, s]
         tol_re = tol_re + 4 * u * cabs[0]
