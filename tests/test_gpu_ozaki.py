@@ -223,3 +223,26 @@ def test_lu_ozaki_one_slice_fewer(api, orc, L):
     b = inputs.truncate_limbs(inputs.exact_rhs(A, xr, xi, L_out=4), L)
     x = host(api.lu_solve(LU, ipiv, dev(b)))
     assert backward_error(orc, A, x, b) <= bound(n, L) * 2.0 ** beta
+
+
+@pytest.mark.parametrize("L", [2, 3])
+@pytest.mark.parametrize("sub_nb", [8, 16, 24])
+def test_lu_ozaki_sub_panel_width(api, orc, L, sub_nb):
+    """Blocks of 128 columns factored as sub-panels of 8, 16 or 24 columns
+    (24: the last sub-panel of every block ragged), Ozaki updates between
+    them: the oracle's pivots, factors within the parity tolerance, backward
+    error <= 16 n u."""
+    n = 200
+    A = inputs.gaussian_matrix(n, L, seed=1)
+    LU, ipiv, info = api.lu_factor(dev(A), method="ozaki", sub_nb=sub_nb)
+    assert int(host(info)[0]) == 0
+    LUo, ipo, _, gap = orc.zgetrf(A)
+    ipg = host(ipiv)
+    mism = np.nonzero(ipg != ipo)[0]
+    assert mism.size == 0, ("pivots differ", mism[:4], ipg[mism[:4]], ipo[mism[:4]], gap[mism[:4]])
+    diff = np.abs((host(LU) - LUo).sum(axis=1)).max()
+    assert diff <= 2.0 ** 10 * n * 2.0 ** -U_EXP[L] * np.abs(A[:, 0]).max() * max(1.0, np.abs(LUo[:, 0]).max())
+    xr, xi = inputs.ones_x_true(n)
+    b = inputs.truncate_limbs(inputs.exact_rhs(A, xr, xi, L_out=4), L)
+    x = host(api.lu_solve(LU, ipiv, dev(b)))
+    assert backward_error(orc, A, x, b) <= bound(n, L)
