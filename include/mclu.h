@@ -59,7 +59,7 @@ typedef struct mclu_opts {
                         /*   32 QD; above S: MCLU_ERR_UNSUPPORTED); 0 = the precision's S     */
   int32_t sub_nb;       /* MCLU_METHOD_OZAKI: width of the sub-panels each block is factored  */
                         /*   in (the columns between them updated by Ozaki products), 1..32; */
-                        /*   0 = 32.  Must be 0 for the other methods                         */
+                        /*   0 = 32 for DD, 16 for TD and QD.  Must be 0 for other methods    */
 } mclu_opts;
 
 /*
