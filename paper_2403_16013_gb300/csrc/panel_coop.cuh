@@ -5,9 +5,10 @@
 // [j0, jend): each CTA keeps a contiguous block of panel rows in shared
 // memory for all nb columns, so a column step needs no kernel launch and no
 // global-memory traffic except the pivot exchange.  Per column j:
-//   1. every CTA computes cabs1 keys of its rows i >= j (column j is up to
-//      date) and writes its best (key, row) to its key slot with a release
-//      stamp (the column);
+//   1. every CTA picks its candidate among its rows i >= j (column j is up
+//      to date) by the leading-limb key k0 (full cabs1 keys only where two
+//      k0 are near) and writes (k0, row) to its key slot with a release
+//      stamp (the column), the candidate's full key with a second stamp;
 //   2. it then applies the pending rank-1 update of column j-1 to the
 //      columns after j (one step of lookahead: only column j was updated
 //      before the keys), first to its best row and to row j, which it
@@ -15,7 +16,8 @@
 //      value under a release flag stamped with the column, then to its other
 //      rows;
 //   3. meanwhile one warp reads every CTA's key slot (bounded waits on the
-//      stamps; same winner p everywhere, ties to the lowest row), waits for
+//      stamps; same winner p everywhere, ties to the lowest row; the full keys
+//      are read only for slots whose k0 are near the largest), waits for
 //      the winner's flag, stages its row and swaps rows j and p where this
 //      CTA owns them (both were published rows, so the update of step 2
 //      never touches them);
@@ -42,7 +44,7 @@ constexpr int COOP_KS = 16;                     // doubles per key slot (one 128
 
 struct CoopWS {
   int *status;    // nonzero: a wait timed out
-  double *kslot;  // [2][G][COOP_KS]: key (L doubles), then row and stamp (two ints), by column parity
+  double *kslot;  // [2][G][COOP_KS] by column parity: full key, row + stamp 1, stamp 2, k0 (slot_ints)
   double *prow;   // [2][G][nb][2L] best row of each CTA, by column parity
   double *srow;   // [2][nb][2L] row j, by column parity
   int *rcp_flag;  // [2G] column stamp (j + 1) of the reciprocal and rows of each slot
@@ -70,6 +72,177 @@ __device__ __forceinline__ bool coop_wait_flag(const int *flag, int v) {
   while (ld_acquire(flag) != v)
     if (clock64() - t0 > COOP_WAIT) return false;
   return true;
+}
+
+// ----------------------------------------------------------- pivot keys --
+// The pivot key of partial pivoting is cabs1 = |Re a| + |Im a| of the
+// multi-component value (pivot_key: an accurate L-limb addition, tens of
+// FP64 instructions in a dependent chain).  The leading limbs decide it
+// almost always, for one FP64 addition: with ulp-nonoverlapping limbs
+// (|x_{l+1}| <= ulp(x_l)) the lower limbs change |Re a| and |Im a| by at
+// most 2^-52 of their leading limbs, and k0 = RN(|Re a_0| + |Im a_0|) adds a
+// rounding of 2^-53, so the exact key K satisfies |K - k0| < 2^-51 k0.  A k0
+// ahead of another by more than 32 ulps (more than 2^-48 relative: ulp(x) >
+// 2^-53 |x|) therefore belongs to the larger exact key; keys within 32 ulps
+// of the largest k0 ("near") are compared in full.
+
+constexpr long long KEY_NEAR_ULPS = 32;
+
+// k0 of row r of panel column c (the pivot column is renormalised, so its
+// limbs are ulp-nonoverlapping); the sign bits are cleared on the integer pipe.
+template <int L>
+__device__ __forceinline__ double cheap_key(const double *sp, int c, int rpc, int r) {
+  const double *d = sp + (size_t)c * 2 * L * rpc + r;
+  const double re = __longlong_as_double(__double_as_longlong(d[0]) & 0x7fffffffffffffffLL);
+  const double im = __longlong_as_double(__double_as_longlong(d[(size_t)L * rpc]) & 0x7fffffffffffffffLL);
+  return __dadd_rn(re, im);
+}
+
+// k0 within KEY_NEAR_ULPS of kmax (both keys are >= 0, k0 <= kmax)
+__device__ __forceinline__ bool key_near(double k0, double kmax) {
+  return order_key(kmax) - order_key(k0) <= KEY_NEAR_ULPS;
+}
+
+// Key slot of one CTA for one column parity (COOP_KS doubles): the full key
+// in doubles 0 .. L-1; the row and stamp 1 in double L (two ints); stamp 2 in
+// double L+1; k0 in double L+2.  Stamp 1 (column + 1) releases k0 and the
+// row, stamp 2 the full key.  The full key of a candidate picked by k0 alone
+// is computed off the critical path and may follow later; it is read only
+// when another CTA's k0 is near.
+template <int L>
+__device__ __forceinline__ int *slot_ints(double *slot) {
+  return reinterpret_cast<int *>(slot + L);
+}
+
+// Publication of this CTA's candidate (one thread): k0 and the row under
+// stamp 1; with has_key, the full key under stamp 2 as well.
+template <int L>
+__device__ __forceinline__ void publish_key_slot(double *slot, int64_t j, int cand, double k0, bool has_key,
+                                                 const double *key) {
+  int *si = slot_ints<L>(slot);
+  slot[L + 2] = k0;
+  si[0] = cand;
+  if (has_key) {
+#pragma unroll
+    for (int l = 0; l < L; l++) slot[l] = key[l];
+  }
+  st_release(si + 1, (int)(j + 1));
+  if (has_key) st_release(si + 2, (int)(j + 1));
+}
+
+// The full key of a candidate chosen by k0 alone, published under stamp 2.
+template <int L>
+__device__ __forceinline__ void publish_full_key(double *slot, int64_t j, const R<L> &key) {
+#pragma unroll
+  for (int l = 0; l < L; l++) slot[l] = key.x[l];
+  st_release(slot_ints<L>(slot) + 2, (int)(j + 1));
+}
+
+struct Winner {
+  int64_t p;  // pivot row (j for a zero column)
+  int part;   // key slot of the winner, -1 if none
+  bool zero;  // every candidate key is zero
+  bool ok;    // false: a wait ran out
+};
+
+// The pivot of column j over all G key slots of parity par, run by one warp:
+// lane l takes slots l, l + 32, ...; their stamps 1 are read together
+// (relaxed) until all carry the column, then one fence orders the reads of
+// k0 and rows after them (an acquire pattern).  The largest k0 (ties: the
+// lowest row) wins unless another slot's k0 is near it; then the full keys of
+// the near slots are awaited (stamp 2, acquire) and compared.
+template <int L>
+__device__ Winner exchange_winner(const CoopWS &cw, int par, int G, int64_t j, int lane) {
+  constexpr int KMAX = COOP_GMAX / 32;
+  const int stamp = (int)(j + 1);
+  unsigned pendk = 0;
+#pragma unroll
+  for (int k = 0; k < KMAX; k++)
+    if (lane + 32 * k < G) pendk |= 1u << k;
+  bool ok = true;
+  const long long t0 = clock64();
+  while (pendk) {
+    unsigned still = 0;
+#pragma unroll
+    for (int k = 0; k < KMAX; k++)
+      if ((pendk >> k) & 1u) {
+        double *slot = cw.kslot + ((size_t)par * G + lane + 32 * k) * COOP_KS;
+        if (ld_relaxed(slot_ints<L>(slot) + 1) != stamp) still |= 1u << k;
+      }
+    pendk = still;
+    if (pendk && clock64() - t0 > COOP_WAIT) {
+      ok = false;
+      break;
+    }
+  }
+  __threadfence();
+  double k0s[KMAX];
+  int rows[KMAX];
+  R<1> bk = invalid_key<1>();
+  int bi = INT_MAX, bq = -1;
+#pragma unroll
+  for (int k = 0; k < KMAX; k++) {
+    k0s[k] = -1.0;
+    rows[k] = INT_MAX;
+    if (ok && lane + 32 * k < G) {
+      double *slot = cw.kslot + ((size_t)par * G + lane + 32 * k) * COOP_KS;
+      k0s[k] = __ldcg(slot + L + 2);
+      rows[k] = __ldcg(slot_ints<L>(slot));
+      R<1> kk;
+      kk.x[0] = k0s[k];
+      if (better<1>(kk, rows[k], bk, bi)) {
+        bk = kk;
+        bi = rows[k];
+        bq = par * G + lane + 32 * k;
+      }
+    }
+  }
+  Winner res{j, -1, true, __all_sync(0xffffffffu, ok)};
+  if (!res.ok) return res;
+  int my = bi, myq = bq;
+  warp_argmax<1>(bk, bi);
+  bool nearx = false;
+  if (bk.x[0] >= 0.0) {
+#pragma unroll
+    for (int k = 0; k < KMAX; k++)
+      if (k0s[k] >= 0.0 && rows[k] != bi && key_near(k0s[k], bk.x[0])) nearx = true;
+  }
+  bool zero = !(bk.x[0] > 0.0);
+  if (__any_sync(0xffffffffu, nearx)) {
+    // full keys of the slots within the window of the largest k0
+    const double kmax = bk.x[0];
+    R<L> fk = invalid_key<L>();
+    int fi = INT_MAX, fq = -1;
+#pragma unroll
+    for (int k = 0; k < KMAX; k++) {
+      if (!ok || k0s[k] < 0.0 || !key_near(k0s[k], kmax)) continue;
+      double *slot = cw.kslot + ((size_t)par * G + lane + 32 * k) * COOP_KS;
+      if (!coop_wait_flag(slot_ints<L>(slot) + 2, stamp)) {
+        ok = false;
+        continue;
+      }
+      R<L> kk;
+#pragma unroll
+      for (int l = 0; l < L; l++) kk.x[l] = __ldcg(slot + l);
+      if (better<L>(kk, rows[k], fk, fi)) {
+        fk = kk;
+        fi = rows[k];
+        fq = par * G + lane + 32 * k;
+      }
+    }
+    res.ok = __all_sync(0xffffffffu, ok);
+    if (!res.ok) return res;
+    my = fi;
+    myq = fq;
+    warp_argmax<L>(fk, fi);
+    bi = fi;
+    zero = !(fk.x[0] > 0.0);
+  }
+  const unsigned own = __ballot_sync(0xffffffffu, my == bi && my != INT_MAX);
+  res.part = own ? __shfl_sync(0xffffffffu, myq, __ffs(own) - 1) : -1;
+  res.zero = zero;
+  res.p = (bi == INT_MAX || zero) ? j : bi;
+  return res;
 }
 
 // Factor panel columns [j0, jend) of rows [j0, n).  CTA b owns rows
@@ -138,8 +311,8 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     const int r = t % nr, c = t / nr;
     stp(r, c, ldz<L>(A, rbeg + r, j0 + c));
   }
-  __shared__ int s_zero, s_next, s_pend, s_ok, s_cand;
-  __shared__ double s_rcp[2 * L], s_key[L];
+  __shared__ int s_zero, s_next, s_pend, s_ok, s_cand, s_fast;
+  __shared__ double s_rcp[2 * L], s_key[L], s_k0;
   if (tid == 0) {
     s_next = 0;
     s_pend = 0;
@@ -153,28 +326,63 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     const double *sprev = su2 + (size_t)(par ^ 1) * RW;  // pivot row of column jc - 1
     const bool pend = s_pend != 0;  // the update of columns jc+1.. from column jc-1 is pending
     const int q = par * G + b;
-    // 1. keys of the rows i >= j of this CTA; its best goes to its key slot
+    // 1. the CTA's candidate among its rows i >= j: the largest k0 (one FP64
+    //    addition per row), unless another row's k0 is near it; then the
+    //    full keys of the near rows decide (s_fast = 0, s_key the full key)
     {
-      R<L> key = invalid_key<L>();
+      R<1> k1 = invalid_key<1>();
       int idx = INT_MAX;
       for (int r = tid; r < nr; r += COOP_T) {
         const int64_t i = rbeg + r;
         if (i < j) continue;
-        const R<L> k = pivot_key<L>(ldp(r, jc));
-        if (better<L>(k, (int)i, key, idx)) {
-          key = k;
+        R<1> k;
+        k.x[0] = cheap_key<L>(sp, jc, rpc, r);
+        if (better<1>(k, (int)i, k1, idx)) {
+          k1 = k;
           idx = (int)i;
         }
       }
-      block_argmax<L>(key, idx, tid, COOP_T);
+      block_argmax<1>(k1, idx, tid, COOP_T);
       if (tid == 0) {
-#pragma unroll
-        for (int l = 0; l < L; l++) s_key[l] = key.x[l];
+        s_k0 = k1.x[0];
         s_cand = idx;
+      }
+      __syncthreads();
+      const double kmax = s_k0;
+      const int c0 = s_cand;
+      bool mynear = false;
+      if (c0 != INT_MAX) {
+        for (int r = tid; r < nr; r += COOP_T) {
+          const int64_t i = rbeg + r;
+          if (i >= j && i != c0 && key_near(cheap_key<L>(sp, jc, rpc, r), kmax)) mynear = true;
+        }
+      }
+      if (__syncthreads_or(mynear)) {
+        R<L> key = invalid_key<L>();
+        int id2 = INT_MAX;
+        for (int r = tid; r < nr; r += COOP_T) {
+          const int64_t i = rbeg + r;
+          if (i < j || !key_near(cheap_key<L>(sp, jc, rpc, r), kmax)) continue;
+          const R<L> k = pivot_key<L>(ldp(r, jc));
+          if (better<L>(k, (int)i, key, id2)) {
+            key = k;
+            id2 = (int)i;
+          }
+        }
+        block_argmax<L>(key, id2, tid, COOP_T);
+        if (tid == 0) {
+#pragma unroll
+          for (int l = 0; l < L; l++) s_key[l] = key.x[l];
+          s_cand = id2;
+          s_fast = 0;
+        }
+      } else if (tid == 0) {
+        s_fast = 1;
       }
       __syncthreads();
     }
     const int cand = s_cand;
+    const bool fast = s_fast != 0;
     const bool has = cand != INT_MAX;                                // uniform over the CTA
     const int cr = has ? (int)(cand - rbeg) : -1;                    // local row of the candidate
     const int jr = (j >= rbeg && j < rend) ? (int)(j - rbeg) : -1;  // local row j
@@ -212,6 +420,8 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
 #pragma unroll
         for (int l = 0; l < L; l++) s_inv[L + l] = x.x[l];
       }
+      if (w == 5 && lane == 0 && has && fast)  // SMSP 1 is free while thread 0 runs the chain
+        publish_full_key<L>(cw.kslot + (size_t)q * COOP_KS, j, pivot_key<L>(ldp(cr, jc)));
       named_sync(1, 128);
       if (act) {
         R<L> x;
@@ -261,74 +471,17 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       }
     }
     if (w == 3) {
-      if (lane == 0) {  // this CTA's best (key, row) to its slot, stamped
-        double *slot = cw.kslot + (size_t)q * COOP_KS;
-#pragma unroll
-        for (int l = 0; l < L; l++) slot[l] = s_key[l];
-        int *si = (int *)(slot + L);
-        si[0] = cand;
-        st_release(si + 1, (int)(j + 1));
+      if (lane == 0) {  // this CTA's candidate (k0, row; the full key if known) to its slot
+        R<L> inv = invalid_key<L>();
+        publish_key_slot<L>(cw.kslot + (size_t)q * COOP_KS, j, cand, has ? s_k0 : -1.0, !has || !fast,
+                            has ? s_key : inv.x);
       }
-      // 3. the winner over all key slots of this column: lane l takes slots
-      //    l, l + 32, ...; their stamps are read together (relaxed) until
-      //    all carry the column, then one fence orders the key reads after
-      //    them (an acquire pattern), and the keys are read together
-      constexpr int KMAX = COOP_GMAX / 32;
-      unsigned pendk = 0;
-#pragma unroll
-      for (int k = 0; k < KMAX; k++)
-        if (lane + 32 * k < G) pendk |= 1u << k;
-      bool ok = true;
-      const long long t0 = clock64();
-      while (pendk) {
-        unsigned still = 0;
-#pragma unroll
-        for (int k = 0; k < KMAX; k++)
-          if ((pendk >> k) & 1u) {
-            const double *slot = cw.kslot + ((size_t)par * G + lane + 32 * k) * COOP_KS;
-            if (ld_relaxed((const int *)(slot + L) + 1) != (int)(j + 1)) still |= 1u << k;
-          }
-        pendk = still;
-        if (pendk && clock64() - t0 > COOP_WAIT) {
-          ok = false;
-          break;
-        }
-      }
-      __threadfence();
-      R<L> bk = invalid_key<L>();
-      int bi = INT_MAX, bq = -1;
-      // keys in batches of KB slots per lane (registers)
-      constexpr int KB = L == 2 ? KMAX : KMAX / 2;
-#pragma unroll
-      for (int k0 = 0; k0 < KMAX; k0 += KB) {
-        if (!ok || lane + 32 * k0 >= G) break;
-        R<L> kk[KB];
-        int ki[KB];
-#pragma unroll
-        for (int k = 0; k < KB; k++) {
-          ki[k] = INT_MAX;
-          if (lane + 32 * (k0 + k) < G) {
-            const double *slot = cw.kslot + ((size_t)par * G + lane + 32 * (k0 + k)) * COOP_KS;
-#pragma unroll
-            for (int l = 0; l < L; l++) kk[k].x[l] = __ldcg(slot + l);
-            ki[k] = __ldcg((const int *)(slot + L));
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < KB; k++)
-          if (lane + 32 * (k0 + k) < G && better<L>(kk[k], ki[k], bk, bi)) {
-            bk = kk[k];
-            bi = ki[k];
-            bq = par * G + lane + 32 * (k0 + k);
-          }
-      }
-      ok = __all_sync(0xffffffffu, ok);
-      const int my = bi, myq = bq;
-      if (ok) warp_argmax<L>(bk, bi);
-      const bool zero = !(bk.x[0] > 0.0);
-      const int64_t p = (bi == INT_MAX || zero) ? j : bi;
-      const unsigned own = __ballot_sync(0xffffffffu, my == bi && my != INT_MAX);
-      const int part = own ? __shfl_sync(0xffffffffu, myq, __ffs(own) - 1) : -1;
+      // 3. the winner over all key slots of this column
+      const Winner win = exchange_winner<L>(cw, par, G, j, lane);
+      bool ok = win.ok;
+      const bool zero = win.zero;
+      const int64_t p = win.p;
+      const int part = win.part;
       const bool own_p = p != j && p >= rbeg && p < rend;
       if (ok && !zero && lane == 0) {
         // the winner's reciprocal and row; row j where this CTA owns row p

@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(COOP_T) k_panel_team(View A, int64_t n, int64_
     const int r = t % nr, c = t / nr;
     stp(r, c, ldz<L>(A, rbeg + r, j0 + c));
   }
-  __shared__ int s_zero, s_pend, s_ok, s_cand;
-  __shared__ double s_rcp[2 * L], s_key[L];
+  __shared__ int s_zero, s_pend, s_ok, s_cand, s_fast, s_near;
+  __shared__ double s_rcp[2 * L], s_key[L], s_k0;
   __shared__ double s_bk[4 * L];
   __shared__ int s_bi[4];
   if (tid == 0) {
@@ -145,44 +145,94 @@ __global__ void __launch_bounds__(COOP_T) k_panel_team(View A, int64_t n, int64_
       const int par = jc & 1;
       double *su = su2 + (size_t)par * RW;  // pivot row of column jc
       const int q = par * G + b;
-      // 1. keys of the rows i >= j of this CTA (column jc is up to date)
+      // 1. the CTA's candidate among its rows i >= j (column jc is up to
+      //    date): the largest k0 (one FP64 addition per row), unless another
+      //    row's k0 is near it; then the full keys of the near rows decide
+      //    (s_fast = 0, s_key the full key)
       {
-        R<L> key = invalid_key<L>();
+        R<1> k1 = invalid_key<1>();
         int idx = INT_MAX;
         for (int r = tid; r < nr; r += 128) {
           const int64_t i = rbeg + r;
           if (i < j) continue;
-          const R<L> k = pivot_key<L>(ldp(r, jc));
-          if (better<L>(k, (int)i, key, idx)) {
-            key = k;
+          R<1> k;
+          k.x[0] = cheap_key<L>(sp, jc, rpc, r);
+          if (better<1>(k, (int)i, k1, idx)) {
+            k1 = k;
             idx = (int)i;
           }
         }
-        warp_argmax<L>(key, idx);
+        warp_argmax<1>(k1, idx);
         if (lane == 0) {
-#pragma unroll
-          for (int l = 0; l < L; l++) s_bk[w * L + l] = key.x[l];
+          s_bk[w * L] = k1.x[0];
           s_bi[w] = idx;
         }
+        if (tid == 0) s_near = 0;
         named_sync(BAR_MAIN, 128);
         if (tid == 0) {
 #pragma unroll
           for (int v = 1; v < 4; v++) {
-            R<L> k;
-#pragma unroll
-            for (int l = 0; l < L; l++) k.x[l] = s_bk[v * L + l];
-            if (better<L>(k, s_bi[v], key, idx)) {
-              key = k;
+            R<1> k;
+            k.x[0] = s_bk[v * L];
+            if (better<1>(k, s_bi[v], k1, idx)) {
+              k1 = k;
               idx = s_bi[v];
             }
           }
-#pragma unroll
-          for (int l = 0; l < L; l++) s_key[l] = key.x[l];
+          s_k0 = k1.x[0];
           s_cand = idx;
         }
         named_sync(BAR_MAIN, 128);
+        const double kmax = s_k0;
+        const int c0 = s_cand;
+        if (c0 != INT_MAX) {
+          for (int r = tid; r < nr; r += 128) {
+            const int64_t i = rbeg + r;
+            if (i >= j && i != c0 && key_near(cheap_key<L>(sp, jc, rpc, r), kmax)) s_near = 1;
+          }
+        }
+        named_sync(BAR_MAIN, 128);
+        const bool near = s_near != 0;
+        if (near) {
+          R<L> key = invalid_key<L>();
+          idx = INT_MAX;
+          for (int r = tid; r < nr; r += 128) {
+            const int64_t i = rbeg + r;
+            if (i < j || !key_near(cheap_key<L>(sp, jc, rpc, r), kmax)) continue;
+            const R<L> k = pivot_key<L>(ldp(r, jc));
+            if (better<L>(k, (int)i, key, idx)) {
+              key = k;
+              idx = (int)i;
+            }
+          }
+          warp_argmax<L>(key, idx);
+          if (lane == 0) {
+#pragma unroll
+            for (int l = 0; l < L; l++) s_bk[w * L + l] = key.x[l];
+            s_bi[w] = idx;
+          }
+          named_sync(BAR_MAIN, 128);
+          if (tid == 0) {
+#pragma unroll
+            for (int v = 1; v < 4; v++) {
+              R<L> k;
+#pragma unroll
+              for (int l = 0; l < L; l++) k.x[l] = s_bk[v * L + l];
+              if (better<L>(k, s_bi[v], key, idx)) {
+                key = k;
+                idx = s_bi[v];
+              }
+            }
+#pragma unroll
+            for (int l = 0; l < L; l++) s_key[l] = key.x[l];
+            s_cand = idx;
+          }
+        }
+        if (tid == 0) s_fast = near ? 0 : 1;
+        named_sync(BAR_MAIN, 128);
       }
       const int cand = s_cand;
+      const bool fast = s_fast != 0;
       const bool has = cand != INT_MAX;                                // uniform over the CTA
       const int cr = has ? (int)(cand - rbeg) : -1;                    // local row of the candidate
       const int jr = (j >= rbeg && j < rend) ? (int)(j - rbeg) : -1;  // local row j
@@ -228,6 +278,8 @@ __global__ void __launch_bounds__(COOP_T) k_panel_team(View A, int64_t n, int64_
             for (int l = 0; l < L; l++) ws.part_rcp[(int64_t)q * 2 * L + w * L + l] = v.x[l];
           }
         }
+        if (w == 2 && lane == 0 && has && fast)  // the full key, off the reciprocal's SMSPs
+          publish_full_key<L>(cw.kslot + (size_t)q * COOP_KS, j, pivot_key<L>(ldp(cr, jc)));
         named_sync(BAR_DONE, 224);  // the update of column jc-1 is complete
         if (w == 2) {
           if (cr >= 0) {
@@ -246,75 +298,19 @@ __global__ void __launch_bounds__(COOP_T) k_panel_team(View A, int64_t n, int64_
         }
         named_arrive(BAR_SWAP, 128);  // rows cr and jr are final: warp 3 may swap them
       } else {
-        // 3. warp 3: this CTA's best (key, row) to its slot, stamped; then
-        //    the winner over all key slots of this column: lane l takes slots
-        //    l, l + 32, ...; their stamps are read together (relaxed) until
-        //    all carry the column, then one fence orders the key reads after
-        //    them (an acquire pattern), and the keys are read together
+        // 3. warp 3: this CTA's candidate (k0, row; the full key when known)
+        //    to its slot, stamped; then the winner over all key slots of this
+        //    column (exchange_winner)
         if (lane == 0) {
-          double *slot = cw.kslot + (size_t)q * COOP_KS;
-#pragma unroll
-          for (int l = 0; l < L; l++) slot[l] = s_key[l];
-          int *si = (int *)(slot + L);
-          si[0] = cand;
-          st_release(si + 1, (int)(j + 1));
+          R<L> inv = invalid_key<L>();
+          publish_key_slot<L>(cw.kslot + (size_t)q * COOP_KS, j, cand, has ? s_k0 : -1.0, !has || !fast,
+                              has ? s_key : inv.x);
         }
-        constexpr int KMAX = COOP_GMAX / 32;
-        unsigned pendk = 0;
-#pragma unroll
-        for (int k = 0; k < KMAX; k++)
-          if (lane + 32 * k < G) pendk |= 1u << k;
-        bool ok = true;
-        const long long t0 = clock64();
-        while (pendk) {
-          unsigned still = 0;
-#pragma unroll
-          for (int k = 0; k < KMAX; k++)
-            if ((pendk >> k) & 1u) {
-              const double *slot = cw.kslot + ((size_t)par * G + lane + 32 * k) * COOP_KS;
-              if (ld_relaxed((const int *)(slot + L) + 1) != (int)(j + 1)) still |= 1u << k;
-            }
-          pendk = still;
-          if (pendk && clock64() - t0 > COOP_WAIT) {
-            ok = false;
-            break;
-          }
-        }
-        __threadfence();
-        R<L> bk = invalid_key<L>();
-        int bi = INT_MAX, bq = -1;
-        // keys in batches of KB slots per lane (registers)
-        constexpr int KB = L == 2 ? KMAX : KMAX / 2;
-#pragma unroll
-        for (int k0 = 0; k0 < KMAX; k0 += KB) {
-          if (!ok || lane + 32 * k0 >= G) break;
-          R<L> kk[KB];
-          int ki[KB];
-#pragma unroll
-          for (int k = 0; k < KB; k++) {
-            ki[k] = INT_MAX;
-            if (lane + 32 * (k0 + k) < G) {
-              const double *slot = cw.kslot + ((size_t)par * G + lane + 32 * (k0 + k)) * COOP_KS;
-#pragma unroll
-              for (int l = 0; l < L; l++) kk[k].x[l] = __ldcg(slot + l);
-              ki[k] = __ldcg((const int *)(slot + L));
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < KB; k++)
-            if (lane + 32 * (k0 + k) < G && better<L>(kk[k], ki[k], bk, bi)) {
-              bk = kk[k];
-              bi = ki[k];
-              bq = par * G + lane + 32 * (k0 + k);
-            }
-        }
-        ok = __all_sync(0xffffffffu, ok);
-        const int my = bi, myq = bq;
-        if (ok) warp_argmax<L>(bk, bi);
-        const bool zero = !(bk.x[0] > 0.0);
-        const int64_t p = (bi == INT_MAX || zero) ? j : bi;
-        const unsigned own = __ballot_sync(0xffffffffu, my == bi && my != INT_MAX);
-        const int part = own ? __shfl_sync(0xffffffffu, myq, __ffs(own) - 1) : -1;
+        const Winner win = exchange_winner<L>(cw, par, G, j, lane);
+        bool ok = win.ok;
+        const bool zero = win.zero;
+        const int64_t p = win.p;
+        const int part = win.part;
         const bool own_p = p != j && p >= rbeg && p < rend;
         if (ok && !zero && lane == 0) {
           // the winner's reciprocal and row; row j where this CTA owns row p

@@ -128,3 +128,28 @@ def test_bounded_wait_runs_out_and_context_survives(api, orc):
     LUo, ipo, info_o, _ = orc.zgetrf(A)
     assert int(host(info)[0]) == info_o == 0
     assert np.array_equal(host(ipiv), ipo)
+
+
+@pytest.mark.parametrize("L", [2, 3])
+@pytest.mark.parametrize("method", ["4m", "ozaki"])
+def test_pivot_near_ties(api, orc, L, method):
+    """Leading limbs drawn from the integers -3..3 (lower limbs random in their
+    canonical range): in the first columns many rows share the leading-limb
+    key |Re a_0| + |Im a_0| inside one CTA and across CTAs (n = 200: 25 CTAs
+    of 8 rows), so the panels' candidate and exchange steps take their
+    full-key path, where only the lower limbs (or the row index, for equal
+    values) decide.  Pivots identical to the oracle's exact cabs1 pivoting."""
+    import numpy as np
+    n = 200
+    rng = np.random.default_rng(91 + L)
+    re = rng.integers(-3, 4, (n, n)).astype(float)
+    im = rng.integers(-3, 4, (n, n)).astype(float)
+    A = inputs._assemble(re, im, L, rng, None)
+    for r in (7, 11):                         # rows 7 and 11: column 0 exactly 3 + 3i (equal keys,
+        A[:, :, 0, r] = 0.0                   # the largest k0; the lower row wins unless another
+        A[0, 0, 0, r] = A[1, 0, 0, r] = 3.0   # row's lower limbs make its key larger)
+    LU, ipiv, LUg, ipg = _factor_compare(api, orc, A, method, nb=0)
+    xr, xi = inputs.ones_x_true(n)
+    b = inputs.truncate_limbs(inputs.exact_rhs(A, xr, xi, L_out=4), L)
+    x = host(api.lu_solve(LU, ipiv, dev(b)))
+    assert backward_error(orc, A, x, b) <= bound(n, L)

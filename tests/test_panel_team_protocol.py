@@ -8,7 +8,9 @@ producers `bar.arrive`, consumers `bar.sync`, a phase completing when the
 barrier's thread count has arrived.  Every path is covered: ordinary columns,
 zero pivots (no elimination), and a timed-out exchange at the first, a middle
 and the last column (the factor team releases the update team at its next go
-signal).  A wait that does not complete within two seconds is a deadlock.
+signal), and columns whose candidate keys are near (the full-key
+comparison adds barrier phases that every warp of the group takes).  A wait
+that does not complete within two seconds is a deadlock.
 """
 import threading
 
@@ -46,7 +48,7 @@ class NamedBarrier:
             self._arrive(n)
 
 
-def run_protocol(nb, zero_cols, err_col):
+def run_protocol(nb, zero_cols, err_col, near_cols=frozenset()):
     B = {k: NamedBarrier(v) for k, v in COUNTS.items()}
     sh = {"ok": 1, "zero": 0}
     errors, lock = [], threading.Lock()
@@ -62,7 +64,11 @@ def run_protocol(nb, zero_cols, err_col):
     def factor_warp(w):
         B["GO"].arrive()
         for jc in range(nb):
-            B["MAIN"].sync()  # keys: warp results
+            B["MAIN"].sync()  # keys: warp results (k0)
+            B["MAIN"].sync()  # keys: the CTA's candidate by k0
+            B["MAIN"].sync()  # keys: near flags
+            if jc in near_cols:
+                B["MAIN"].sync()  # full keys of the near rows: warp results
             B["MAIN"].sync()  # keys: CTA result
             if w < 3:
                 if w < 2:
@@ -114,7 +120,8 @@ def test_panel_team_protocol_deadlock_free(nb):
     cases = [((), -1), ((0,), -1), ((nb - 1,), -1), (tuple(range(nb)), -1),
              ((), 0), ((), nb - 1), ((1,), nb // 2)]
     for zero_cols, err_col in cases:
-        assert run_protocol(nb, set(zero_cols), err_col) == [], (nb, zero_cols, err_col)
+        for near in (set(), {0, nb - 1}, set(range(0, nb, 2))):
+            assert run_protocol(nb, set(zero_cols), err_col, near) == [], (nb, zero_cols, err_col, near)
 
 
 def test_protocol_model_detects_a_missing_arrival():
@@ -134,7 +141,7 @@ def test_protocol_model_detects_a_missing_arrival():
     assert out == ["deadlock"]
 
 
-def run_coop_protocol(nb, zero_cols, err_col):
+def run_coop_protocol(nb, zero_cols, err_col, near_cols=frozenset()):
     """k_panel_coop: __syncthreads (all 8 warps), bar 1 (warps 0, 1, 4, 5:
     the reciprocal), bar 2 (warps 0, 1, 2, 7: release of the flag), bar 3
     (warps 2 and 7 arrive, warp 3 waits before its swap)."""
@@ -145,7 +152,11 @@ def run_coop_protocol(nb, zero_cols, err_col):
     def warp(w):
         B["ALL"].sync()                       # rows loaded
         for jc in range(nb):
-            B["ALL"].sync(); B["ALL"].sync()  # keys: block argmax
+            B["ALL"].sync(); B["ALL"].sync()  # keys: block argmax of k0
+            B["ALL"].sync()                   # keys: the candidate by k0
+            B["ALL"].sync()                   # keys: __syncthreads_or of the near flags
+            if jc in near_cols:
+                B["ALL"].sync(); B["ALL"].sync()  # full keys of the near rows: block argmax
             B["ALL"].sync()                   # keys: the CTA's candidate
             if w in (0, 1, 4, 5):
                 B["B1"].sync(); B["B1"].sync()
@@ -190,4 +201,5 @@ def test_panel_coop_protocol_deadlock_free(nb):
     cases = [((), -1), ((0,), -1), ((nb - 1,), -1), (tuple(range(nb)), -1),
              ((), 0), ((), nb - 1), ((1,), nb // 2)]
     for zero_cols, err_col in cases:
-        assert run_coop_protocol(nb, set(zero_cols), err_col) == [], (nb, zero_cols, err_col)
+        for near in (set(), {0, nb - 1}, set(range(0, nb, 2))):
+            assert run_coop_protocol(nb, set(zero_cols), err_col, near) == [], (nb, zero_cols, err_col, near)
