@@ -39,3 +39,25 @@ def exact_diff(orc, g: np.ndarray, o: np.ndarray) -> np.ndarray:
     g, o: [L, count] limb-major arrays."""
     V = np.concatenate([g, -o], axis=0).T.copy()
     return orc.exact_sum_rows(V, 1)[:, 0]
+
+
+def planes_diff(orc, G: np.ndarray, O: np.ndarray) -> np.ndarray:
+    """|value(G) - value(O)| per element, the difference of all limbs of both
+    taken exactly (superaccumulator) and rounded to binary64.  G, O: planes
+    [2, L, cols, ld] or samples [s, 2, L] (limb axis given by the layout).
+    Subtracting limb by limb and summing in binary64 is not exact: two valid
+    L-limb forms of one value (e.g. 2 - 2^-52 + 0.4 2^-52 against
+    2 - 0.6 2^-52) round their limb differences at the 2^-105 level."""
+    G = np.asarray(G, np.float64)
+    O = np.asarray(O, np.float64)
+    if G.ndim == 4:        # [2, L, cols, ld]
+        L = G.shape[1]
+        g = np.moveaxis(G, 1, -1).reshape(-1, L)
+        o = np.moveaxis(O, 1, -1).reshape(-1, O.shape[1])
+        out_shape = (G.shape[0], G.shape[2], G.shape[3])
+    else:                  # [s, 2, L]
+        g = G.reshape(-1, G.shape[2])
+        o = O.reshape(-1, O.shape[2])
+        out_shape = G.shape[:2]
+    V = np.ascontiguousarray(np.concatenate([g, -o], axis=1))
+    return np.abs(orc.exact_sum_rows(V, 1)[:, 0]).reshape(out_shape)

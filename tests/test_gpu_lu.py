@@ -9,7 +9,7 @@ pivots, differing only in rounding order).
 import numpy as np
 import pytest
 
-from gpu_util import backward_error, bound, dev, host
+from gpu_util import backward_error, bound, dev, host, planes_diff
 from helpers import U_EXP
 from lu_cases import known_factor_case
 from paper_2403_16013_gb300 import inputs
@@ -38,7 +38,7 @@ def _factor_compare(api, orc, A, method, nb=0):
     assert mism.size == 0, ("pivots differ", mism[:4], ipg[mism[:4]], ipo[mism[:4]], gap[mism[:4]])
     LUg = host(LU)
     scale = np.abs(A[:, 0]).max()
-    diff = np.abs((LUg - LUo).sum(axis=1)).max()
+    diff = planes_diff(orc, LUg, LUo).max()
     assert diff <= 2.0 ** 10 * n * 2.0 ** -U_EXP[L] * scale * max(1.0, np.abs(LUo[:, 0]).max()), diff
     return LU, ipiv, LUg, ipg
 
@@ -65,7 +65,7 @@ def test_blocked_ragged(api, orc, L, method):
     x = host(api.lu_solve(LU, ipiv, dev(b)))
     assert backward_error(orc, A, x, b) <= bound(n, L)
     xo = orc.zgetrs(LUg, ipg, b)
-    assert np.abs((x - xo).sum(axis=1)).max() <= 2.0 ** 12 * n * 2.0 ** -U_EXP[L]
+    assert planes_diff(orc, x, xo).max() <= 2.0 ** 12 * n * 2.0 ** -U_EXP[L]
 
 
 @pytest.mark.parametrize("L", [2, 4])
@@ -89,7 +89,7 @@ def test_solve_conjugate_transpose(api, orc, L):
     c = inputs.complex_gaussian_vector(n, L, seed=3)
     y = host(api.lu_solve(LU, ipiv, dev(c), trans="C"))
     yo = orc.zgetrs(host(LU), host(ipiv), c, "C")
-    assert np.abs((y - yo).sum(axis=1)).max() <= 2.0 ** 12 * n * 2.0 ** -U_EXP[L] * np.abs(yo[:, 0]).max()
+    assert planes_diff(orc, y, yo).max() <= 2.0 ** 12 * n * 2.0 ** -U_EXP[L] * np.abs(yo[:, 0]).max()
 
 
 def test_zero_column_info(api, orc):
@@ -113,7 +113,7 @@ def test_multiple_rhs_and_padding(api, orc):
     LUo, ipo, _, _ = orc.zgetrf(A)
     assert np.array_equal(host(ipiv), ipo)
     Xo = orc.zgetrs(LUo, ipo, Bm)
-    assert np.abs((X - Xo).sum(axis=1)).max() <= 2.0 ** 12 * n * 2.0 ** -U_EXP[L] * np.abs(Xo[:, 0]).max()
+    assert planes_diff(orc, X, Xo).max() <= 2.0 ** 12 * n * 2.0 ** -U_EXP[L] * np.abs(Xo[:, 0]).max()
 
 
 def test_bounded_wait_runs_out_and_context_survives(api, orc):
