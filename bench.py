@@ -59,7 +59,7 @@ LIMBS = {"dd": 2, "td": 3, "qd": 4}
 # 0.625e12 FP64 operations per second (2 per clock per SM at 2.07 GHz).
 FP64_OPS_PEAK = 0.625e12
 # Ozaki-scheme engine: slices S per precision; kept pairs p + q <= S - 1.
-OZAKI_S = {"dd": 14, "td": 24, "qd": 32}
+OZAKI_S = {"dd": 16, "td": 24, "qd": 32}
 # DRAM traffic of the trailing-update kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of the first trailing update of
 # the n = 4096 DD step: n2 = 3968 rows and columns, K = 256 realified).  It is

@@ -55,7 +55,7 @@ typedef struct mclu_opts {
   int32_t nb;           /* panel width K of Sec. 3 (block size NDIM); 0 = 64 (128 for Ozaki); */
                         /*   1..256                                                           */
   int32_t method;       /* MCLU_METHOD_*; default MCLU_METHOD_4M                             */
-  int32_t ozaki_slices; /* MCLU_METHOD_OZAKI: slices kept per operand, 1..S (S = 14 DD, 24 TD, */
+  int32_t ozaki_slices; /* MCLU_METHOD_OZAKI: slices kept per operand, 1..S (S = 16 DD, 24 TD, */
                         /*   32 QD; above S: MCLU_ERR_UNSUPPORTED); 0 = the precision's S     */
   int32_t sub_nb;       /* MCLU_METHOD_OZAKI: width of the sub-panels each block is factored  */
                         /*   in (the columns between them updated by Ozaki products), 1..32; */
@@ -152,7 +152,7 @@ int zgemm_qd(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const d
  * zgemm_{dd,td,qd}_ex: zgemm_* with the number of Ozaki slices (Sec. 2.3:
  * the number of divisions of each operand, which sets the accuracy of the
  * Ozaki-scheme product).
- *   ozaki_slices  MCLU_METHOD_OZAKI: 1..S slices kept per operand (S = 14
+ *   ozaki_slices  MCLU_METHOD_OZAKI: 1..S slices kept per operand (S = 16
  *                 DD, 24 TD, 32 QD), the digit pairs p + q <= ozaki_slices - 1
  *                 multiplied; 0 = S; above S: MCLU_ERR_UNSUPPORTED.  Ignored
  *                 by the other methods.
@@ -189,8 +189,8 @@ int zadjoint_rank1_qd(int64_t n, const double *lambda, const double *x, double *
  *          [ceil(rows/32)][S][Npad][64], Npad = 2 cols rounded up to N
  *          (N = 32 DD, 16 TD/QD); element (r, j): row 2j holds [Re | -Im] and
  *          row 2j+1 [Im | Re] at K index r%32 | 32 + r%32; E int32[cols].
- * Digit p of x is a_p with x ~ 2^E sum_p a_p 2^(-beta (p+1)), beta = 8, 7, 7
- * and S = 14, 24, 32 for DD, TD, QD.  slices and E are caller-owned device
+ * Digit p of x is a_p with x ~ 2^E sum_p a_p 2^(-beta (p+1)), beta = 7
+ * and S = 16, 24, 32 for DD, TD, QD.  slices and E are caller-owned device
  * buffers of those sizes.
  */
 int zozaki_split_dd(int side, int64_t rows, int64_t cols, const double *X, int64_t ld, void *slices, int32_t *E,

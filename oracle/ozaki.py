@@ -19,7 +19,7 @@ from fractions import Fraction
 
 import numpy as np
 
-CFG = {2: (8, 14), 3: (7, 24), 4: (7, 32)}   # L -> (beta, S)
+CFG = {2: (7, 16), 3: (7, 24), 4: (7, 32)}   # L -> (beta, S)
 
 
 def leading_exponent(x: float) -> int | None:

@@ -336,6 +336,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   auto laswp = [&](int64_t k0, int64_t k1, int64_t c0, int64_t c1, int64_t x0, int64_t x1) -> int {
     const int64_t ncols = (c1 - c0) - (x1 - x0);
     if (ncols <= 0 || k1 <= k0) return 0;
+    if (k1 - k0 > COOP_NB_MAX) return (int)cudaErrorInvalidValue;  // one pivot per thread of k_laswp_gather
     ProfScope ps(PK_LASWP, s);
     const size_t lsm = laswp_smem((int)(k1 - k0));
     if (lsm > 48 * 1024) {

@@ -384,16 +384,20 @@ __global__ void __launch_bounds__(PANEL_T *PANEL_T)
 // other than [x0, x1) (x0 = x1: none excluded; the excluded range lies inside
 // [c0, c1)), numbered c' = 0 .. ncols - 1, all 2L planes.  The swaps only
 // touch rows [k0, k1) and their partners p >= k, so their product is a
-// permutation of at most 2 (k1 - k0) rows: warp 0 composes it in shared
-// memory (slot s < nb is row k0 + s, later slots hold partner rows below k1;
-// org[s] = the row whose content ends in slot s's row), then every CTA
-// gathers the moved rows of its LASWP_C columns into shared memory and writes
-// them back permuted.  Rows in [k0, k1) are contiguous in a column
-// (coalesced); partner rows cost one sector each.
+// permutation of at most 2 (k1 - k0) rows (slot s < nb is row k0 + s, later
+// slots hold the distinct partner rows at or below k1; org[s] = the row whose
+// content ends in slot s's row).  Every CTA builds it in shared memory: each
+// thread finds whether its partner row occurs earlier (the first occurrence
+// gets a slot, numbered by a block prefix sum), then one thread applies the
+// transpositions in order as swaps of org entries (two shared-memory reads
+// and writes per swap).  Then each CTA gathers the moved rows of its
+// LASWP_C columns into shared memory and writes them back permuted.  Rows in
+// [k0, k1) are contiguous in a column (coalesced); partner rows cost one
+// sector each.  k1 - k0 <= 256 (one pivot per thread).
 constexpr int LASWP_C = 16;  // columns per CTA
 
 inline size_t laswp_smem(int nb) {
-  return (size_t)2 * nb * (2 * sizeof(int) + LASWP_C * sizeof(double)) + (size_t)nb * sizeof(int) + 16;
+  return (size_t)2 * nb * (2 * sizeof(int) + LASWP_C * sizeof(double)) + (size_t)4 * nb * sizeof(int) + 16;
 }
 
 template <int L>
@@ -405,49 +409,66 @@ __global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t k0, int64_
   int *dst = reinterpret_cast<int *>(vals + (size_t)2 * nb * LASWP_C);  // [2 nb]
   int *org = dst + 2 * nb;                                 // [2 nb]
   int *piv = org + 2 * nb;                                 // [nb] the pivots, read once
-  __shared__ int s_cnt;
-  const int tid = threadIdx.x, lane = tid & 31;
-  for (int t = tid; t < nb; t += 256) {
-    dst[t] = (int)(k0 + t);
-    org[t] = (int)(k0 + t);
-    piv[t] = ipiv[k0 + t] - 1;
-  }
-  if (tid == 0) s_cnt = 0;
+  int *fidx = piv + nb;                                    // [nb] first pivot with the same partner row
+  int *pslot = fidx + nb;                                  // [nb] slot of a first partner occurrence
+  int *slotof = pslot + nb;                                // [nb] slot of the row swapped with row k0 + k
+  __shared__ int s_cnt, s_wsum[8];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid < nb) piv[tid] = ipiv[k0 + tid] - 1;
   __syncthreads();
-  if (tid < 32) {
-    int cnt = 0;  // partner rows below k1 seen so far (slots nb .. nb + cnt - 1)
-    for (int k = 0; k < nb; k++) {
-      const int kk = (int)k0 + k;
-      const int p = piv[k];
-      if (p == kk) continue;
-      int sp;
-      if (p < k1) {
-        sp = p - (int)k0;
-      } else {
-        sp = -1;
-        for (int base = 0; base < cnt && sp < 0; base += 32) {
-          const bool hit = base + lane < cnt && dst[nb + base + lane] == p;
-          const unsigned m = __ballot_sync(0xffffffffu, hit);
-          if (m) sp = nb + base + __ffs(m) - 1;
+  int first = 0;
+  if (tid < nb) {
+    const int p = piv[tid];
+    int f = -1;
+    if (p >= k1) {  // a partner row below the panel's rows: its first occurrence
+      f = tid;
+      for (int t2 = 0; t2 < tid; t2++)
+        if (piv[t2] == p) {
+          f = t2;
+          break;
         }
-        if (sp < 0) {
-          sp = nb + cnt;
-          if (lane == 0) {
-            dst[sp] = p;
-            org[sp] = p;
-          }
-          cnt++;
-        }
-        __syncwarp();
-      }
-      if (lane == 0) {
-        const int t = org[k];
-        org[k] = org[sp];
-        org[sp] = t;
-      }
-      __syncwarp();
+      first = f == tid;
     }
-    if (lane == 0) s_cnt = cnt;
+    fidx[tid] = f;
+    dst[tid] = (int)k0 + tid;
+    org[tid] = (int)k0 + tid;
+  }
+  int incl = first;  // block prefix sum of the first occurrences (8 warps)
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  if (lane == 31) s_wsum[w] = incl;
+  __syncthreads();
+  int base = 0;
+  for (int v = 0; v < w; v++) base += s_wsum[v];
+  if (first) {
+    const int sl = nb + base + incl - 1;
+    pslot[tid] = sl;
+    dst[sl] = piv[tid];
+    org[sl] = piv[tid];
+  }
+  if (tid == 0) {
+    int tot = 0;
+    for (int v = 0; v < 8; v++) tot += s_wsum[v];
+    s_cnt = tot;
+  }
+  __syncthreads();
+  if (tid < nb) {
+    const int p = piv[tid];
+    slotof[tid] = p < k1 ? p - (int)k0 : pslot[fidx[tid]];
+  }
+  __syncthreads();
+  if (tid == 0) {  // the transpositions in order
+    for (int k = 0; k < nb; k++) {
+      const int sb = slotof[k];
+      if (sb != k) {
+        const int t = org[k];
+        org[k] = org[sb];
+        org[sb] = t;
+      }
+    }
   }
   __syncthreads();
   const int T = nb + s_cnt;

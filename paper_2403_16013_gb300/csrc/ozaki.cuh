@@ -21,9 +21,10 @@
 //  Products (tcgen05.mma kind::f16, M = 128, N = 32 or 16, K = 16).  Slice
 //  pairs (p, q) with p + q <= S - 1 are kept; pair products with the same
 //  p + q = d go to one TMEM fp32 accumulator D_d.  Every digit product is an
-//  integer of at most 2^14 (beta = 8) or 2^12 (beta = 7) and a K = 64 chunk
-//  has at most S pairs per diagonal, so every partial sum is an integer below
-//  2^24: the fp32 accumulation is exact.
+//  integer of at most 2^12 (beta = 7), a K = 64 chunk has at most S pairs per
+//  diagonal, and chunks_per_fold chunks accumulate before the epilogue reads
+//  them, so every partial sum is an integer of at most 2^24: the fp32
+//  accumulation is exact.
 //
 //  Epilogue (integer ALU only).  F = sum_d D_d 2^(beta (S-1-d)) is folded into
 //  a register-resident fixed-point integer; the product is
@@ -60,7 +61,7 @@ struct Cfg;
 // TD/QD.
 template <>
 struct Cfg<2> {
-  static constexpr int BETA = 8, S = 14, N = 32, FW = 5, TW = 4, RW = 6, GS = 5, EW = 16, EF = 1;
+  static constexpr int BETA = 7, S = 16, N = 32, FW = 5, TW = 4, RW = 6, GS = 6, EW = 16, EF = 1;
 };
 template <>
 struct Cfg<3> {
@@ -79,6 +80,19 @@ constexpr int default_slices() {
 }
 
 constexpr int KC = 64;         // realified K per chunk (32 complex columns of A)
+
+// K chunks whose products accumulate in TMEM before the epilogue folds them:
+// the largest c with c KC S 2^(2 beta - 2) <= 2^24, so that every partial
+// sum of a diagonal (at most S digit products of at most 2^(2 beta - 2) per K
+// index) is an integer of at most 2^24 and the fp32 accumulation stays exact.
+// DD (beta 7, S 16): 4 chunks, i.e. a whole trailing update of nb = 128; TD,
+// QD: 2.
+template <int L>
+__host__ __device__ constexpr int chunks_per_fold() {
+  return (int)((1LL << 24) / ((long long)KC * Cfg<L>::S * (1LL << (2 * Cfg<L>::BETA - 2))));
+}
+static_assert(chunks_per_fold<2>() == 4 && chunks_per_fold<3>() == 2 && chunks_per_fold<4>() == 2,
+              "fold groups of K chunks");
 constexpr int NB_MAX = KC / 2; // complex panel width per chunk
 constexpr int BM = 128;        // tile rows (TMEM lanes)
 constexpr int NST = 4;         // A pipeline stages
@@ -660,6 +674,7 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
               int64_t n, int nchunks, int Mpad, int Npad, const int *Ea, const int *Eb, int *status, int Se) {
   using CF = Cfg<L>;
   constexpr int S = CF::S, N = CF::N, BETA_B = CF::BETA, FW = CF::FW, RW = CF::RW;
+  constexpr int CPF = chunks_per_fold<L>();
   constexpr int A_BYTES = BM * KC * 2;  // 16 KB
   constexpr int B_TILE = N * KC * 2;    // 4 KB or 2 KB (multiples of 1024 B)
   constexpr int B_BYTES = S * B_TILE;
@@ -735,10 +750,14 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // --------------------------------------------- MMA
-      uint32_t a_it = 0, r = 0;
+      uint32_t a_it = 0, r = 0, g = 0;  // r: K chunks (B pipeline), g: fold groups (TMEM)
       for (int64_t t = blockIdx.x; t < total && !s_err; t += gridDim.x) {
         for (int c = 0; c < nchunks; c++, r++) {
-          if (!mbar_wait(&bar_accempty, (r & 1) ^ 1) || !mbar_wait(&bar_bfull, r & 1)) {
+          // a fold group of CPF chunks accumulates in TMEM: its first chunk
+          // overwrites the diagonals once the epilogue has read the previous
+          // group, its last chunk signals the diagonal groups
+          const bool gfirst = c % CPF == 0, glast = c % CPF == CPF - 1 || c == nchunks - 1;
+          if ((gfirst && !mbar_wait(&bar_accempty, (g & 1) ^ 1)) || !mbar_wait(&bar_bfull, r & 1)) {
             s_err = 3;
             break;
           }
@@ -764,15 +783,17 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
               const uint32_t idesc = umma_idesc_n(nn);
 #pragma unroll
               for (int ks = 0; ks < KC / 16; ks++)
-                umma_bf16(d, umma_desc(a0 + ks * 32), umma_desc(b0 + ks * 32), idesc, (p > 0 || ks > 0) ? 1u : 0u);
+                umma_bf16(d, umma_desc(a0 + ks * 32), umma_desc(b0 + ks * 32), idesc,
+                          (p > 0 || ks > 0 || !gfirst) ? 1u : 0u);
             }
             umma_commit(&bar_aempty[st]);
             // diagonals of the group ending at p are complete: let the
             // epilogue fold them while the later slices multiply
-            if ((p + 1) % CF::GS == 0 || p == Se - 1) umma_commit(&bar_grp[p / CF::GS]);
+            if (glast && ((p + 1) % CF::GS == 0 || p == Se - 1)) umma_commit(&bar_grp[p / CF::GS]);
           }
           if (s_err) break;
           umma_commit(&bar_bempty);
+          if (glast) g++;
         }
       }
     }
@@ -782,7 +803,8 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
     const int etid = threadIdx.x - 64;  // 0 .. 32 * EPI_WARPS - 1
     const Scratch sc{reinterpret_cast<uint32_t *>(sA + NST * A_BYTES) + etid, EPI_WARPS * 32};
     const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * NH);
-    uint32_t r = 0;
+    uint32_t g = 0;  // fold groups
+    const int ngroups = (nchunks + CPF - 1) / CPF;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
       const int mtile = (int)(t / nt), ntile = (int)(t % nt);
       uint32_t F[NH][FW];
@@ -791,10 +813,11 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
 #pragma unroll
         for (int w = 0; w < FW; w++) F[cc][w] = 0;
       bool ok = true;
-      for (int c = 0; c < nchunks; c++, r++) {
-        // diagonal d sits in TMEM columns [d N, d N + N); each group is
-        // folded as soon as its commit barrier completes
-        if (!fold_diagonals<L, NH, 0>(F, tbase, bar_grp, r & 1, lane, Se)) {
+      for (int gi = 0; gi < ngroups; gi++, g++) {
+        // diagonal d sits in TMEM columns [d N, d N + N), summed over the
+        // group's K chunks; each group of diagonals is folded as soon as its
+        // commit barrier completes
+        if (!fold_diagonals<L, NH, 0>(F, tbase, bar_grp, g & 1, lane, Se)) {
           if (lane == 0) s_err = 5;
           ok = false;
           break;

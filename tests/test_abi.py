@@ -42,11 +42,11 @@ def test_argument_validation_without_gpu(lib):
     assert B.zgemm("dd", 2, 0, 1, 1, 1, 8, 1, 8, 1, 8, 1) == -1
     assert B.zgemm("dd", 0, 9, 1, 1, 1, 8, 1, 8, 1, 8, 1) == -2
     assert B.zgemm_ex("dd", 0, B.METHOD_OZAKI, -1, 1, 1, 1, 8, 1, 8, 1, 8, 1) == -3
-    assert B.zgemm_ex("dd", 0, B.METHOD_OZAKI, 15, 1, 1, 1, 8, 1, 8, 1, 8, 1) == B.ERR_UNSUPPORTED
+    assert B.zgemm_ex("dd", 0, B.METHOD_OZAKI, 17, 1, 1, 1, 8, 1, 8, 1, 8, 1) == B.ERR_UNSUPPORTED
     assert B.zgemm_ex("qd", 0, B.METHOD_OZAKI, 33, 1, 1, 1, 8, 1, 8, 1, 8, 1) == B.ERR_UNSUPPORTED
     assert B.zgemm_ex("td", 0, B.METHOD_4M, 0, -1, 1, 1, 8, 1, 8, 1, 8, 1) == -4     # m, one place further
     assert B.zgemm_ex("td", 0, B.METHOD_4M, 0, 4, 1, 1, 8, 1, 8, 1, 8, 1) == -8      # lda < m
-    assert B.zgetrf_ex("dd", 4, 8, 4, 8, 0, method=B.METHOD_OZAKI, ozaki_slices=15) == B.ERR_UNSUPPORTED
+    assert B.zgetrf_ex("dd", 4, 8, 4, 8, 0, method=B.METHOD_OZAKI, ozaki_slices=17) == B.ERR_UNSUPPORTED
     assert B.zgetrf_ex("td", 4, 8, 4, 8, 0, method=B.METHOD_OZAKI, ozaki_slices=-2) == -6
     assert B.zadjoint_rank1("dd", 4, 8, 8, 8, 2) == -5
     assert B.vec_op(99, 2, 4, 8, 8, 8) == -1

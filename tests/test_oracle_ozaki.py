@@ -2,7 +2,8 @@
 the digits reconstruct the fixed-point integer exactly, stay in their ranges,
 and the sliced value is within L units of 2^(E - beta S) of the exact element
 (Fraction).  Also the exactness premise of the tensor-core accumulation: for
-K = 64 the sum of S diagonal pair products of extreme digits stays <= 2^24."""
+K = 64 the sum of S diagonal pair products of extreme digits stays <= 2^24,
+over the number of K chunks accumulated before each fold as well."""
 from fractions import Fraction
 
 import numpy as np
@@ -47,3 +48,8 @@ def test_accumulation_stays_exact_in_fp32(L):
     dmax = 1 << (beta - 1)
     K = 64
     assert S * K * dmax * dmax <= 1 << 24       # worst diagonal of one K = 64 chunk
+    # the K chunks accumulated in TMEM before the epilogue folds them
+    # (chunks_per_fold in ozaki.cuh): 4 for DD, 2 for TD and QD
+    cpf = {2: 4, 3: 2, 4: 2}[L]
+    assert cpf * S * K * dmax * dmax <= 1 << 24 < (cpf + 1) * S * K * dmax * dmax
+    assert beta * S >= 53 * L + 6               # slices cover the precision with margin
