@@ -117,6 +117,45 @@ int zgetrf_dd_noalloc(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t 
 int64_t zgetrf_dd_noalloc_max_n(void);
 
 /*
+ * dgetrf_{dd,td,qd}, dgetrf_{dd,td,qd}_ex: LU factorisation with partial
+ * pivoting of a REAL L-limb matrix, P A = L U (the real multi-component LU
+ * of Secs. 1 and 3 that the complex one extends).
+ *   A     device, L column-major planes (plane l at A + l*lda*n), n x n,
+ *         leading dimension lda; overwritten by L (unit diagonal not
+ *         stored) and U
+ *   n, lda, ipiv, info, opts, stream  as in zgetrf_*_ex
+ * Pivot key |a| in L-limb arithmetic, ties to the lowest row.  The real
+ * planes run through the complex path as the real part of a complex matrix
+ * with a zero imaginary part (cabs1(a + 0i) = |a|; every imaginary part
+ * stays exactly zero): a workspace of 2 L n^2 doubles is allocated
+ * stream-ordered, and the cost is that of the complex factorisation.
+ */
+int dgetrf_dd(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream);
+int dgetrf_td(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream);
+int dgetrf_qd(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream);
+int dgetrf_dd_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
+                 void *stream);
+int dgetrf_td_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
+                 void *stream);
+int dgetrf_qd_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
+                 void *stream);
+
+/*
+ * dgetrs_{dd,td,qd}: solve with the factors of dgetrf_* (Sec. 4).
+ *   trans 'N': A X = B;  'T': A^T X = B
+ *   B     device, L planes of n x nrhs, leading dimension ldb (plane stride
+ *         ldb*nrhs); overwritten by X
+ *   the other arguments as in zgetrs_*; a workspace of 2 L n (n + nrhs)
+ *   doubles is allocated stream-ordered.
+ */
+int dgetrs_dd(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda, const int32_t *ipiv, double *B,
+              int64_t ldb, void *stream);
+int dgetrs_td(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda, const int32_t *ipiv, double *B,
+              int64_t ldb, void *stream);
+int dgetrs_qd(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda, const int32_t *ipiv, double *B,
+              int64_t ldb, void *stream);
+
+/*
  * zgetrs_{dd,td,qd}: solve with the factors of zgetrf (Sec. 4: "forward and
  * backward substitutions").
  *   trans 'N': A X = B  (apply P, unit-lower forward, upper back substitution)

@@ -71,6 +71,39 @@ def lu_solve(LU: torch.Tensor, ipiv: torch.Tensor, Bm: torch.Tensor, trans: str 
     return X
 
 
+def _check_real_planes(T: torch.Tensor, name: str):
+    if not isinstance(T, torch.Tensor) or not T.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if T.dtype != torch.float64 or T.dim() != 3 or T.shape[0] not in (2, 3, 4) or not T.is_contiguous():
+        raise ValueError(f"{name} must be contiguous float64 limb planes of shape [L, cols, ld], L in 2..4; "
+                         f"got {tuple(T.shape)} {T.dtype}")
+
+
+def dlu_factor(A: torch.Tensor, method: str = "4m", nb: int = 0, ozaki_slices: int = 0, sub_nb: int = 0):
+    """Real P A = L U.  A: limb planes [L, n, lda].  Returns (LU, ipiv, info)."""
+    _check_real_planes(A, "A")
+    n, lda = A.shape[1], A.shape[2]
+    LU = A.clone()
+    ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    rc = B.dgetrf_ex({2: "dd", 3: "td", 4: "qd"}[A.shape[0]], n, LU.data_ptr(), lda, ipiv.data_ptr(),
+                     info.data_ptr(), nb, METHODS[method], ozaki_slices, _stream(), sub_nb=sub_nb)
+    B.check(rc, "dgetrf")
+    return LU, ipiv[:n], info
+
+
+def dlu_solve(LU: torch.Tensor, ipiv: torch.Tensor, Bm: torch.Tensor, trans: str = "N"):
+    """Solve A X = B ('N') or A^T X = B ('T') with the factors of dlu_factor; B: [L, nrhs, ldb]."""
+    _check_real_planes(LU, "LU")
+    _check_real_planes(Bm, "B")
+    X = Bm.clone()
+    n, lda = LU.shape[1], LU.shape[2]
+    rc = B.dgetrs({2: "dd", 3: "td", 4: "qd"}[LU.shape[0]], trans, n, X.shape[1], LU.data_ptr(), lda,
+                  ipiv.data_ptr(), X.data_ptr(), X.shape[2], _stream())
+    B.check(rc, "dgetrs")
+    return X
+
+
 def zgemm(A: torch.Tensor, Bm: torch.Tensor, C: torch.Tensor | None = None, method: str = "4m",
           ozaki_slices: int = 0):
     """C = A B (C is None) or C - A B (returns a new tensor).  ozaki_slices:

@@ -34,6 +34,12 @@ def _declare(lib):
         f.argtypes, f.restype = [i64, vp, i64, vp, vp, C.POINTER(MCLUOpts), vp], ci
         f = getattr(lib, f"zgetrs_{s}")
         f.argtypes, f.restype = [cc, i64, i64, vp, i64, vp, vp, i64, vp], ci
+        f = getattr(lib, f"dgetrf_{s}")
+        f.argtypes, f.restype = [i64, vp, i64, vp, vp], ci
+        f = getattr(lib, f"dgetrf_{s}_ex")
+        f.argtypes, f.restype = [i64, vp, i64, vp, vp, C.POINTER(MCLUOpts), vp], ci
+        f = getattr(lib, f"dgetrs_{s}")
+        f.argtypes, f.restype = [cc, i64, i64, vp, i64, vp, vp, i64, vp], ci
         f = getattr(lib, f"zgemm_{s}")
         f.argtypes, f.restype = [ci, ci, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp], ci
         f = getattr(lib, f"zgemm_{s}_ex")
@@ -133,6 +139,16 @@ def zgetrf_ex(prec: str, n, A, lda, ipiv, info, nb=0, method=METHOD_4M, ozaki_sl
 
 def zgetrf_dd_noalloc(n, A, lda, ipiv, info, stream=None) -> int:
     return load().zgetrf_dd_noalloc(n, A, lda, ipiv, info, _stream(stream))
+
+
+def dgetrf_ex(prec: str, n, A, lda, ipiv, info, nb=0, method=METHOD_4M, ozaki_slices=0, stream=None,
+              sub_nb=0) -> int:
+    o = MCLUOpts(nb, method, ozaki_slices, sub_nb)
+    return getattr(load(), f"dgetrf_{prec}_ex")(n, A, lda, ipiv, info, C.byref(o), _stream(stream))
+
+
+def dgetrs(prec: str, trans: str, n, nrhs, A, lda, ipiv, B, ldb, stream=None) -> int:
+    return getattr(load(), f"dgetrs_{prec}")(trans.encode(), n, nrhs, A, lda, ipiv, B, ldb, _stream(stream))
 
 
 def zgetrs(prec: str, trans: str, n, nrhs, A, lda, ipiv, B, ldb, stream=None) -> int:

@@ -603,6 +603,66 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
   return 0;
 }
 
+// Real (one-plane) factorisation and solve: the real L-limb planes enter the
+// complex path as the real part of complex planes with a zero imaginary part
+// (a complex workspace of 2L planes, stream-ordered).  The complex pivot key
+// cabs1(a + 0i) = |a| is the real one, and every imaginary part stays exactly
+// zero through the factorisation (each product with a zero factor is an exact
+// zero, every sum of zeros is exact), so the factors are the real parts.
+template <int L>
+int dgetrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
+           cudaStream_t s) {
+  if (n < 0) return -1;
+  if (n > 0 && Ap == nullptr) return -2;
+  if (lda < std::max<int64_t>(1, n)) return -3;
+  if (n > 0 && ipiv == nullptr) return -4;
+  if (n == 0) return getrf<L>(0, Ap, lda, ipiv, info, opts, s);
+  if (n > INT32_MAX - 1) return -1;
+  Workspace w;
+  MCLU_TRY(w.alloc((size_t)2 * L * n * n * sizeof(double), s));
+  View Z{(double *)w.p, n, n * n};
+  const unsigned grid = (unsigned)cdiv(n * n, 256);
+  k_real_planes<L><<<grid, 256, 0, s>>>(Ap, lda, Z, n, n, true);
+  MCLU_LAUNCHED();
+  const int rc = getrf<L>(n, Z.p, n, ipiv, info, opts, s);
+  if (rc) return rc;
+  k_real_planes<L><<<grid, 256, 0, s>>>(Ap, lda, Z, n, n, false);
+  MCLU_LAUNCHED();
+  return 0;
+}
+
+// Solve with the factors of dgetrf: 'N' A X = B, 'T' A^T X = B (the complex
+// 'C' solve on the zero-imaginary embedding).  B: L planes, n x nrhs,
+// leading dimension ldb.
+template <int L>
+int dgetrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, const int32_t *ipiv, double *Bp,
+           int64_t ldb, cudaStream_t s) {
+  if (trans != 'N' && trans != 'n' && trans != 'T' && trans != 't') return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0) return -3;
+  if (n > 0 && Ap == nullptr) return -4;
+  if (lda < std::max<int64_t>(1, n)) return -5;
+  if (n > 0 && ipiv == nullptr) return -6;
+  if (n > 0 && nrhs > 0 && Bp == nullptr) return -7;
+  if (ldb < std::max<int64_t>(1, n)) return -8;
+  if (n == 0 || nrhs == 0) return 0;
+  if (n > INT32_MAX - 1) return -2;
+  Workspace w;
+  const size_t za = (size_t)2 * L * n * n, zb = (size_t)2 * L * n * nrhs;
+  MCLU_TRY(w.alloc((za + zb) * sizeof(double), s));
+  View ZA{(double *)w.p, n, n * n}, ZB{(double *)w.p + za, n, n * nrhs};
+  k_real_planes<L><<<(unsigned)cdiv(n * n, 256), 256, 0, s>>>(const_cast<double *>(Ap), lda, ZA, n, n, true);
+  MCLU_LAUNCHED();
+  k_real_planes<L><<<(unsigned)cdiv(n * nrhs, 256), 256, 0, s>>>(Bp, ldb, ZB, n, nrhs, true);
+  MCLU_LAUNCHED();
+  const char ct = (trans == 'N' || trans == 'n') ? 'N' : 'C';
+  const int rc = getrs<L>(ct, n, nrhs, ZA.p, n, ipiv, ZB.p, n, s);
+  if (rc) return rc;
+  k_real_planes<L><<<(unsigned)cdiv(n * nrhs, 256), 256, 0, s>>>(Bp, ldb, ZB, n, nrhs, false);
+  MCLU_LAUNCHED();
+  return 0;
+}
+
 template <int L>
 int gemm(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const double *Ap, int64_t lda, const double *Bp,
          int64_t ldb, double *Cp, int64_t ldc, cudaStream_t s, int ozaki_slices = 0) {
@@ -717,6 +777,17 @@ int vec_op(int op, int64_t count, const double *x, const double *y, double *z, c
   }                                                                                                              \
   extern "C" int zgetrf_##SUF(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream) {                 \
     return mclu::getrf<LIMBS>(n, A, lda, ipiv, nullptr, nullptr, (cudaStream_t)stream);                         \
+  }                                                                                                              \
+  extern "C" int dgetrf_##SUF##_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info,             \
+                                   const mclu_opts *opts, void *stream) {                                       \
+    return mclu::dgetrf<LIMBS>(n, A, lda, ipiv, info, opts, (cudaStream_t)stream);                              \
+  }                                                                                                              \
+  extern "C" int dgetrf_##SUF(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream) {                 \
+    return mclu::dgetrf<LIMBS>(n, A, lda, ipiv, nullptr, nullptr, (cudaStream_t)stream);                        \
+  }                                                                                                              \
+  extern "C" int dgetrs_##SUF(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda,                \
+                              const int32_t *ipiv, double *B, int64_t ldb, void *stream) {                      \
+    return mclu::dgetrs<LIMBS>(trans, n, nrhs, A, lda, ipiv, B, ldb, (cudaStream_t)stream);                     \
   }                                                                                                              \
   extern "C" int zgetrs_##SUF(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda,                \
                               const int32_t *ipiv, double *B, int64_t ldb, void *stream) {                      \

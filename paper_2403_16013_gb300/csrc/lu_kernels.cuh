@@ -1436,6 +1436,28 @@ __global__ void k_rank1_adjoint(View lam, View x, View Ab, int64_t n) {
   stz<L>(Ab, i, j, z_neg<L>(z_mul<L>(l, xj)));
 }
 
+// Real L-limb matrices (L column-major planes, plane l at R + l ld_r cols)
+// and the complex planes the factorisation runs on: to_complex copies the
+// real planes into the real part of Z and zeroes its imaginary part; the
+// reverse copies the real part of Z back.  One thread per element and plane.
+template <int L>
+__global__ void k_real_planes(double *R, int64_t ld_r, View Z, int64_t rows, int64_t cols, bool to_complex) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * cols) return;
+  const int64_t i = t % rows, j = t / rows;
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    double *r = R + (int64_t)l * ld_r * cols + j * ld_r + i;
+    double *zr = Z.p + (int64_t)l * Z.ps + j * Z.ld + i;
+    if (to_complex) {
+      *zr = *r;
+      Z.p[(int64_t)(L + l) * Z.ps + j * Z.ld + i] = 0.0;
+    } else {
+      *r = *zr;
+    }
+  }
+}
+
 // Reports a nonzero tensor-core pipeline status through info (< 0).
 static __global__ void k_merge_status(const int *status, int *info) {
   if (*status) *info = -1000 - *status;

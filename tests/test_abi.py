@@ -48,6 +48,10 @@ def test_argument_validation_without_gpu(lib):
     assert B.zgemm_ex("td", 0, B.METHOD_4M, 0, 4, 1, 1, 8, 1, 8, 1, 8, 1) == -8      # lda < m
     assert B.zgetrf_ex("dd", 4, 8, 4, 8, 0, method=B.METHOD_OZAKI, ozaki_slices=17) == B.ERR_UNSUPPORTED
     assert B.zgetrf_ex("td", 4, 8, 4, 8, 0, method=B.METHOD_OZAKI, ozaki_slices=-2) == -6
+    assert B.dgetrf_ex("td", -1, 8, 1, 8, 0) == -1
+    assert B.dgetrf_ex("qd", 4, 8, 3, 8, 0) == -3
+    assert B.dgetrs("dd", "C", 4, 1, 8, 4, 8, 8, 4) == -1          # real solves take 'N' or 'T'
+    assert B.dgetrs("dd", "T", 4, 1, 8, 4, 8, 8, 2) == -8
     assert B.zadjoint_rank1("dd", 4, 8, 8, 8, 2) == -5
     assert B.vec_op(99, 2, 4, 8, 8, 8) == -1
     assert B.vec_op(0, 5, 4, 8, 8, 8) == -2
