@@ -98,7 +98,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="mclu", choices=["mclu", "reference"])
     p.add_argument("--prec", default="dd", choices=["dd", "td", "qd"])
-    p.add_argument("--method", default="ozaki", choices=["4m", "3m", "unblocked", "ozaki"])
+    p.add_argument("--method", default="ozaki", choices=["4m", "3m", "unblocked", "ozaki", "strassen"])
     p.add_argument("--n", type=int, default=4096)
     p.add_argument("--nb", type=int, default=0, help="block width (0: 128 for ozaki, 64 otherwise)")
     p.add_argument("--no-e2e", action="store_true")
@@ -399,7 +399,7 @@ def run_sweep(args):
     ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     points = [("unblocked", 0)]
-    for method in ("4m", "3m", "ozaki"):
+    for method in ("4m", "3m", "strassen", "ozaki"):
         for nb in (16, 32, 64, 96, 128, 192, 256):
             points.append((method, nb))
     for method, nb in points:
@@ -535,12 +535,14 @@ def zgemm_point(ctx, prec, method, m, n, k, reps, A, B, fp64=None, slices=0) -> 
                            "peak_source": src + " bf16 burst", "traffic": None,
                            "kernel": f"k_oz_gemm<{L},0> (+ split kernels)"}
     else:
-        ops = float(m) * n * k * (3 if method == "3m" else 4) * I_REAL[prec]
+        # Strassen: 7 of the 8 block products of 3M (one level of Winograd's variant)
+        ops = float(m) * n * k * {"3m": 3.0, "4m": 4.0, "strassen": 3.0 * 7 / 8}[method] * I_REAL[prec]
         peak, src = fp64_peak(fp64)
         ach = ops / (kern_ms * 1e-3)
         out["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T FP64-ops/s",
                            "frac": ach / peak, "peak_source": src, "traffic": None,
-                           "kernel": f"k_gemm<{L},{'3M' if method == '3m' else '4M'},0> (+ k_resum for 3M)"}
+                           "kernel": f"k_gemm<{L},{'4M' if method == '4m' else '3M'},0> (+ k_resum for 3M"
+                                     f"{', block sums and combinations for Strassen' if method == 'strassen' else ''})"}
     return out
 
 
@@ -597,7 +599,7 @@ def run_zgemm(args):
         L = LIMBS[prec]
         A = torch.from_numpy(inputs.gaussian_matrix(1024, L, seed=1)).cuda()
         B = torch.from_numpy(inputs.gaussian_matrix(1024, L, seed=2)).cuda()
-        for method in ("4m", "3m", "ozaki"):
+        for method in ("4m", "3m", "strassen", "ozaki"):
             r = zgemm_point(ctx, prec, method, 1024, 1024, 1024, max(1, args.steps), A, B, fp64=fp64)
             r["workload"] = "gaussian limbs 1024^3"
             print(json.dumps(r), flush=True)

@@ -45,9 +45,11 @@ enum {
   MCLU_METHOD_3M = 1,        /* 3M matrix product by Eq. (3): T1, T2, T3 then Re = T1 - T2,      */
                              /*   Im = T3 - (T1 + T2)                                              */
   MCLU_METHOD_UNBLOCKED = 2, /* "Normal LU" of Sec. 3: right-looking row elimination, no GEMM    */
-  MCLU_METHOD_OZAKI = 3      /* Ozaki-scheme update (Sec. 2.3): exact bf16 slice products on the */
+  MCLU_METHOD_OZAKI = 3,     /* Ozaki-scheme update (Sec. 2.3): exact bf16 slice products on the */
                              /*   tensor cores; block width nb <= 256 (default 128), factored as */
-                             /*   32-column sub-panels with Ozaki updates between them           */
+                             /*   sub-panels with Ozaki updates between them                     */
+  MCLU_METHOD_STRASSEN = 4   /* Strassen form (Sec. 2.3): one level of Winograd's variant, seven */
+                             /*   3M block products instead of eight on the FP64 pipe            */
 };
 
 /* Optional parameters of the *_ex factorisation calls (NULL = defaults). */

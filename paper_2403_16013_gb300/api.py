@@ -13,7 +13,8 @@ import torch
 from . import binding as B
 
 LIMBS = B.LIMBS
-METHODS = {"4m": B.METHOD_4M, "3m": B.METHOD_3M, "unblocked": B.METHOD_UNBLOCKED, "ozaki": B.METHOD_OZAKI}
+METHODS = {"4m": B.METHOD_4M, "3m": B.METHOD_3M, "unblocked": B.METHOD_UNBLOCKED, "ozaki": B.METHOD_OZAKI,
+           "strassen": B.METHOD_STRASSEN}
 
 
 def _prec(T: torch.Tensor) -> str:

@@ -13,7 +13,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmclu.so")
 
-METHOD_4M, METHOD_3M, METHOD_UNBLOCKED, METHOD_OZAKI = 0, 1, 2, 3
+METHOD_4M, METHOD_3M, METHOD_UNBLOCKED, METHOD_OZAKI, METHOD_STRASSEN = 0, 1, 2, 3, 4
 ERR_UNSUPPORTED = 100000
 LIMBS = {"dd": 2, "td": 3, "qd": 4}
 

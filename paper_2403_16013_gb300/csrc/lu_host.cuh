@@ -228,6 +228,123 @@ int launch_resum(View X, View S, int64_t m, int64_t k, cudaStream_t s) {
   return 0;
 }
 
+// A plain block product C = C - A B (beta) or A B on the FP64 pipe with the
+// 3M (Eq. 3, pre-sums into SA / SB, m x k and k x n L-limb planes) or the 4M
+// (Eq. 1) kernel.
+template <int L>
+int block_product(bool m3, bool beta, View A, View B, View C, double *SA, double *SB, int64_t m, int64_t n,
+                  int64_t k, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return 0;
+  View sa{nullptr, 0, 0}, sb{nullptr, 0, 0};
+  if (m3) {
+    sa = View{SA, m, m * k};
+    sb = View{SB, k, k * n};
+    int rc = launch_resum<L>(A, sa, m, k, s);
+    if (rc) return rc;
+    rc = launch_resum<L>(B, sb, k, n, s);
+    if (rc) return rc;
+  }
+  return launch_gemm<L>(m3 ? MCLU_METHOD_3M : MCLU_METHOD_4M, beta, A, B, C, sa, sb, m, n, k, s);
+}
+
+template <int L>
+int launch_madd(View X, View Y, View Z, int64_t m, int64_t n, bool sub, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return 0;
+  k_madd<L><<<(unsigned)cdiv(m * n, 256), 256, 0, s>>>(X, Y, Z, m, n, sub);
+  MCLU_LAUNCHED();
+  return 0;
+}
+
+// C = C - A B (m x n, inner k) by one level of Winograd's variant of
+// Strassen's algorithm (Sec. 2.3: the Strassen form of the complex matrix
+// product): the even part of the three dimensions splits into 2 x 2 blocks,
+//   S1 = A21 + A22, S2 = S1 - A11, S3 = A11 - A21, S4 = A12 - S2,
+//   T1 = B12 - B11, T2 = B22 - T1, T3 = B22 - B12, T4 = T2 - B21,
+//   P1 = A11 B11, P2 = A12 B21, P3 = S4 B22, P4 = A22 T4,
+//   P5 = S1 T1, P6 = S2 T2, P7 = S3 T3,
+//   C11 -= P1 + P2, C12 -= P1 + P6 + P5 + P3,
+//   C21 -= P1 + P6 + P7 - P4, C22 -= P1 + P6 + P7 + P5,
+// seven block products (3M or 4M kernel) instead of eight; the block sums
+// are accurate L-limb additions and each C block takes its sum in one
+// accumulator.  An odd last k index, row and column are peeled off as plain
+// products.  Workspace: stream-ordered.
+template <int L>
+int strassen_update(bool m3, View A, View B, View C, int64_t m, int64_t n, int64_t k, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return 0;
+  const int64_t m2 = m / 2, n2 = n / 2, k2 = k / 2;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t zs = al((size_t)2 * L * m2 * k2 * 8), zt = al((size_t)2 * L * k2 * n2 * 8),
+               zp = al((size_t)2 * L * m2 * n2 * 8);
+  const size_t za = al((size_t)L * std::max<int64_t>(m, 1) * std::max<int64_t>(k, 1) * 8),
+               zb = al((size_t)L * std::max<int64_t>(k, 1) * std::max<int64_t>(n, 1) * 8);
+  Workspace w;
+  const bool split = m2 > 0 && n2 > 0 && k2 > 0;
+  MCLU_TRY(w.alloc((split ? 4 * zs + 4 * zt + 7 * zp : 0) + za + zb, s));
+  char *cur = (char *)w.p;
+  double *SA = (double *)cur;
+  double *SB = (double *)(cur + za);
+  cur += za + zb;
+  if (split) {
+    auto blk = [&](View X, int64_t r0, int64_t c0) { return View{X.p + c0 * X.ld + r0, X.ld, X.ps}; };
+    const View A11 = blk(A, 0, 0), A12 = blk(A, 0, k2), A21 = blk(A, m2, 0), A22 = blk(A, m2, k2);
+    const View B11 = blk(B, 0, 0), B12 = blk(B, 0, n2), B21 = blk(B, k2, 0), B22 = blk(B, k2, n2);
+    const View C11 = blk(C, 0, 0), C12 = blk(C, 0, n2), C21 = blk(C, m2, 0), C22 = blk(C, m2, n2);
+    View Sv[4], Tv[4], Pv[7];
+    for (int q = 0; q < 4; q++, cur += zs) Sv[q] = View{(double *)cur, m2, m2 * k2};
+    for (int q = 0; q < 4; q++, cur += zt) Tv[q] = View{(double *)cur, k2, k2 * n2};
+    for (int q = 0; q < 7; q++, cur += zp) Pv[q] = View{(double *)cur, m2, m2 * n2};
+    {
+      ProfScope ps(PK_OTHER, s);
+      int rc = launch_madd<L>(A21, A22, Sv[0], m2, k2, false, s);       // S1
+      if (!rc) rc = launch_madd<L>(Sv[0], A11, Sv[1], m2, k2, true, s);  // S2
+      if (!rc) rc = launch_madd<L>(A11, A21, Sv[2], m2, k2, true, s);    // S3
+      if (!rc) rc = launch_madd<L>(A12, Sv[1], Sv[3], m2, k2, true, s);  // S4
+      if (!rc) rc = launch_madd<L>(B12, B11, Tv[0], k2, n2, true, s);    // T1
+      if (!rc) rc = launch_madd<L>(B22, Tv[0], Tv[1], k2, n2, true, s);  // T2
+      if (!rc) rc = launch_madd<L>(B22, B12, Tv[2], k2, n2, true, s);    // T3
+      if (!rc) rc = launch_madd<L>(Tv[1], B21, Tv[3], k2, n2, true, s);  // T4
+      if (rc) return rc;
+    }
+    {
+      ProfScope ps(PK_GEMM, s);
+      const View X[7] = {A11, A12, Sv[3], A22, Sv[0], Sv[1], Sv[2]};
+      const View Y[7] = {B11, B21, B22, Tv[3], Tv[0], Tv[1], Tv[2]};
+      for (int q = 0; q < 7; q++) {
+        const int rc = block_product<L>(m3, false, X[q], Y[q], Pv[q], SA, SB, m2, n2, k2, s);
+        if (rc) return rc;
+      }
+    }
+    {
+      ProfScope ps(PK_OTHER, s);
+      const unsigned g = (unsigned)cdiv(m2 * n2, 256);
+      const View P1 = Pv[0], P2 = Pv[1], P3 = Pv[2], P4 = Pv[3], P5 = Pv[4], P6 = Pv[5], P7 = Pv[6];
+      k_mcombine<L><<<g, 256, 0, s>>>(C11, P1, P2, P2, P2, 2, 0u, m2, n2);
+      MCLU_LAUNCHED();
+      k_mcombine<L><<<g, 256, 0, s>>>(C12, P1, P6, P5, P3, 4, 0u, m2, n2);
+      MCLU_LAUNCHED();
+      k_mcombine<L><<<g, 256, 0, s>>>(C21, P1, P6, P7, P4, 4, 8u, m2, n2);
+      MCLU_LAUNCHED();
+      k_mcombine<L><<<g, 256, 0, s>>>(C22, P1, P6, P7, P5, 4, 0u, m2, n2);
+      MCLU_LAUNCHED();
+    }
+  }
+  // peeled parts: the odd k index on the even block, the odd row, the odd column
+  ProfScope ps(PK_GEMM, s);
+  const int64_t me = 2 * m2, ne = 2 * n2, ke = 2 * k2;
+  if (!split) return block_product<L>(m3, true, A, B, C, SA, SB, m, n, k, s);
+  int rc = 0;
+  if (k > ke)
+    rc = block_product<L>(m3, true, View{A.p + ke * A.ld, A.ld, A.ps}, View{B.p + ke, B.ld, B.ps}, C, SA, SB, me,
+                          ne, k - ke, s);
+  if (!rc && m > me)
+    rc = block_product<L>(m3, true, View{A.p + me, A.ld, A.ps}, B, View{C.p + me, C.ld, C.ps}, SA, SB, m - me, n, k,
+                          s);
+  if (!rc && n > ne)
+    rc = block_product<L>(m3, true, A, View{B.p + ne * B.ld, B.ld, B.ps}, View{C.p + ne * C.ld, C.ld, C.ps}, SA, SB,
+                          me, n - ne, k, s);
+  return rc;
+}
+
 // Right-looking blocked LU (Sec. 3): for each panel of width nb: factor the
 // panel (pivot search, swap, scale, rank-1 steps), swap the rows left and
 // right of it, TRSM for U12, and the trailing update A22 <- A22 - L21 U12.
@@ -249,7 +366,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   if (opts) {
     if (opts->nb < 0 || opts->nb > 256) return -6;
     if (opts->nb) nb = opts->nb;
-    if (opts->method < MCLU_METHOD_4M || opts->method > MCLU_METHOD_OZAKI) return -6;
+    if (opts->method < MCLU_METHOD_4M || opts->method > MCLU_METHOD_STRASSEN) return -6;
     method = opts->method;
     if (opts->sub_nb < 0 || opts->sub_nb > oz::NB_MAX) return -6;
     if (opts->sub_nb != 0 && method != MCLU_METHOD_OZAKI) return -6;
@@ -445,9 +562,14 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
         rc = launch_resum<L>(U12, SU, jb, n2, s);
         if (rc) return rc;
       }
-      ProfScope ps(PK_GEMM, s);
-      int rc = ozk ? oz::gemm<L>(true, L21, U12, A22, n2, n2, jb, oz_ws, oz_status, s, note_launch, Se)
-                   : launch_gemm<L>(method, true, L21, U12, A22, SL, SU, n2, n2, jb, s);
+      int rc;
+      if (method == MCLU_METHOD_STRASSEN) {
+        rc = strassen_update<L>(true, L21, U12, A22, n2, n2, jb, s);
+      } else {
+        ProfScope ps(PK_GEMM, s);
+        rc = ozk ? oz::gemm<L>(true, L21, U12, A22, n2, n2, jb, oz_ws, oz_status, s, note_launch, Se)
+                 : launch_gemm<L>(method, true, L21, U12, A22, SL, SU, n2, n2, jb, s);
+      }
       if (rc) return rc;
     }
   }
@@ -667,7 +789,9 @@ template <int L>
 int gemm(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const double *Ap, int64_t lda, const double *Bp,
          int64_t ldb, double *Cp, int64_t ldc, cudaStream_t s, int ozaki_slices = 0) {
   if (beta_mode != 0 && beta_mode != 1) return -1;
-  if (method != MCLU_METHOD_4M && method != MCLU_METHOD_3M && method != MCLU_METHOD_OZAKI) return -2;
+  if (method != MCLU_METHOD_4M && method != MCLU_METHOD_3M && method != MCLU_METHOD_OZAKI &&
+      method != MCLU_METHOD_STRASSEN)
+    return -2;
   // ozaki_slices: 0 (default) or 1 .. S, checked by the caller
   const int Se = ozaki_slices ? ozaki_slices : oz::default_slices<L>();
   if (m < 0) return -3;
@@ -689,6 +813,18 @@ int gemm(int beta_mode, int method, int64_t m, int64_t n, int64_t k, const doubl
     MCLU_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
     ProfScope ps(PK_GEMM, s);
     return oz::gemm<L>(beta_mode == 1, A, B, C, m, n, k, w.p, status, s, note_launch, Se);
+  }
+  if (method == MCLU_METHOD_STRASSEN) {
+    if (beta_mode == 0) {  // C = A B: zero C, C -= A B, negate (exact)
+      for (int pl = 0; pl < 2 * L; pl++)
+        MCLU_TRY(cudaMemset2DAsync(C.p + (int64_t)pl * C.ps, C.ld * sizeof(double), 0, m * sizeof(double), n, s));
+    }
+    if (k == 0) return 0;
+    int rc = strassen_update<L>(true, A, B, C, m, n, k, s);
+    if (rc || beta_mode == 1) return rc;
+    k_mneg<L><<<(unsigned)cdiv(m * n, 256), 256, 0, s>>>(C, m, n);
+    MCLU_LAUNCHED();
+    return 0;
   }
   if (method == MCLU_METHOD_3M && k > 0) {
     MCLU_TRY(w.alloc((size_t)(m * k + k * n) * L * sizeof(double) + 512, s));

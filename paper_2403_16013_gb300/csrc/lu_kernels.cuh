@@ -1436,22 +1436,72 @@ __global__ void k_rank1_adjoint(View lam, View x, View Ab, int64_t n) {
   stz<L>(Ab, i, j, z_neg<L>(z_mul<L>(l, xj)));
 }
 
+// Strassen-Winograd blocks (Sec. 2.3): Z = X + sgn Y for m x n complex
+// blocks, each part an accurate L-limb addition (rounded to L limbs).
+template <int L>
+__global__ void k_madd(View X, View Y, View O, int64_t m, int64_t n, bool sub) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * n) return;
+  const int64_t i = t % m, j = t / m;
+  const Z<L> x = ldz<L>(X, i, j), y = ldz<L>(Y, i, j);
+  stz<L>(O, i, j, sub ? z_sub<L>(x, y) : z_add<L>(x, y));
+}
+
+// C = C - sum_q s_q P_q over up to four m x n product blocks (s_q = +1 or
+// -1, bit q of neg set for -1), summed on the leveled accumulator with one
+// rounding to L limbs: the combination steps of Winograd's variant.
+template <int L>
+__global__ void k_mcombine(View C, View P0, View P1, View P2, View P3, int np, unsigned neg, int64_t m, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * n) return;
+  const int64_t i = t % m, j = t / m;
+  const Z<L> c = ldz<L>(C, i, j);
+  Acc<L> re, im;
+  re.set(c.re);
+  im.set(c.im);
+  const View P[4] = {P0, P1, P2, P3};
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    if (q >= np) break;
+    const Z<L> v = ldz<L>(P[q], i, j);
+    const bool sgn = ((neg >> q) & 1u) == 0;  // subtract s_q P_q: negate when s_q = +1
+    Acc<L> a, b;
+    a.set(v.re);
+    b.set(v.im);
+    re.add_acc(a, sgn);
+    im.add_acc(b, sgn);
+  }
+  Z<L> z;
+  z.re = re.result();
+  z.im = im.result();
+  stz<L>(C, i, j, z);
+}
+
+// Z = -Z for an m x n complex block (exact: sign bits only).
+template <int L>
+__global__ void k_mneg(View O, int64_t m, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * n) return;
+  const int64_t i = t % m, j = t / m;
+  stz<L>(O, i, j, z_neg<L>(ldz<L>(O, i, j)));
+}
+
 // Real L-limb matrices (L column-major planes, plane l at R + l ld_r cols)
 // and the complex planes the factorisation runs on: to_complex copies the
 // real planes into the real part of Z and zeroes its imaginary part; the
 // reverse copies the real part of Z back.  One thread per element and plane.
 template <int L>
-__global__ void k_real_planes(double *R, int64_t ld_r, View Z, int64_t rows, int64_t cols, bool to_complex) {
+__global__ void k_real_planes(double *R, int64_t ld_r, View Zc, int64_t rows, int64_t cols, bool to_complex) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows * cols) return;
   const int64_t i = t % rows, j = t / rows;
 #pragma unroll
   for (int l = 0; l < L; l++) {
     double *r = R + (int64_t)l * ld_r * cols + j * ld_r + i;
-    double *zr = Z.p + (int64_t)l * Z.ps + j * Z.ld + i;
+    double *zr = Zc.p + (int64_t)l * Zc.ps + j * Zc.ld + i;
     if (to_complex) {
       *zr = *r;
-      Z.p[(int64_t)(L + l) * Z.ps + j * Z.ld + i] = 0.0;
+      Zc.p[(int64_t)(L + l) * Zc.ps + j * Zc.ld + i] = 0.0;
     } else {
       *r = *zr;
     }

@@ -137,3 +137,65 @@ def test_adjoint_full_size_properties(api, orc):
     ex = orc.exact_entries(lam_col, xh, rows, cols, C=np.ascontiguousarray(gA), sign=1)   # Abar + lambda x^H
     mag = np.abs(gb[:, 0]).max() * np.abs(x[:, 0]).max()
     assert np.abs(ex[:, :, 0]).max() <= 8 * 2.0 ** -U_EXP[L] * mag
+
+
+def test_adjoint_qd_finite_differences_n2048(api, orc):
+    """The adjoint workload at its size: n = 2048 DD, b = A (1 + i), c complex
+    Gaussian (seed 4), loss Re(c^H x); 64 sampled entries (i, j) and both the
+    real and the imaginary perturbation of A_ij.  The central difference of
+    the loss with step t = 2^-60 is evaluated exactly (rational arithmetic) by
+    Sherman-Morrison, x(A + t e_i e_j^T) = x - t w x_j / (1 + t w_j),
+    w = A^{-1} e_i, from QD solutions x and w (the library's QD factorisation
+    of the same matrix, 64 right-hand sides in one solve, a path checked
+    against the oracle on its own) and the exact dot products c^H w (oracle
+    superaccumulator).  The DD gradient must agree within 2^-70 of max|Abar|."""
+    import torch
+    n = 2048
+    A = inputs.gaussian_matrix(n, 2, seed=4)
+    xr, xi = inputs.ones_x_true(n)
+    b = inputs.truncate_limbs(inputs.exact_rhs(A, xr, xi, L_out=4), 2)
+    c = inputs.complex_gaussian_vector(n, 2, seed=4)
+    c[:, 1:] = 0.0                                # the loss sees the binary64 value of c
+    x, gA, gb = _grads(api, A, b, c)
+    # the same matrix and right-hand side in QD (zero-padded limbs), factored on the GPU
+    A4 = np.zeros((2, 4, n, n))
+    A4[:, :2] = A
+    b4 = np.zeros((2, 4, 1, n))
+    b4[:, :2] = b
+    LU4, ip4, info4 = api.lu_factor(dev(A4), method="ozaki")
+    x4 = host(api.lu_solve(LU4, ip4, dev(b4)))
+    rng = np.random.default_rng(9)
+    rows, cols = rng.integers(0, n, 64), rng.integers(0, n, 64)
+    E = np.zeros((2, 4, 64, n))
+    E[0, 0, np.arange(64), rows] = 1.0
+    W = host(api.lu_solve(LU4, ip4, dev(E)))      # w_s = A^{-1} e_{i_s}, QD, [2, 4, 64, n]
+    torch.cuda.synchronize()
+    assert int(host(info4)[0]) == 0
+    # s_k = c^H w_k exactly: the row c^H (conjugated) times the columns of W
+    cH = np.zeros((2, 4, n, 1))
+    cH[0, 0, :, 0] = c[0, 0, 0]
+    cH[1, 0, :, 0] = -c[1, 0, 0]
+    sdot = orc.exact_entries(cH, W, np.zeros(64, np.int64), np.arange(64, dtype=np.int64))  # [64, 2, 4]
+    fr = lambda v: sum((Fraction(float(t)) for t in v), Fraction(0))
+    h = Fraction(1, 2 ** 60)
+    gscale = np.abs(gA[:, 0]).max()
+    worst = 0.0
+    for k, (i, j) in enumerate(zip(rows, cols)):
+        s = (fr(sdot[k, 0]), fr(sdot[k, 1]))
+        xj = (fr(x4[0, :, 0, j]), fr(x4[1, :, 0, j]))
+        wj = (fr(W[0, :, k, j]), fr(W[1, :, k, j]))
+        for part in (0, 1):                       # perturb Re(A_ij) or Im(A_ij)
+            t = (h, Fraction(0)) if part == 0 else (Fraction(0), h)
+            fs = []
+            for sgn in (1, -1):
+                ts = (sgn * t[0], sgn * t[1])
+                den = (1 + ts[0] * wj[0] - ts[1] * wj[1], ts[0] * wj[1] + ts[1] * wj[0])
+                num = (ts[0] * xj[0] - ts[1] * xj[1], ts[0] * xj[1] + ts[1] * xj[0])
+                d2 = den[0] ** 2 + den[1] ** 2
+                fs.append(((num[0] * den[0] + num[1] * den[1]) / d2, (num[1] * den[0] - num[0] * den[1]) / d2))
+            # L(t) - L(-t) = -Re(s (f(t) - f(-t))), Re(c^H x) cancels
+            df = (fs[0][0] - fs[1][0], fs[0][1] - fs[1][1])
+            fd = float(-(s[0] * df[0] - s[1] * df[1]) / (2 * h))
+            g = gA[part, :, j, i].sum()
+            worst = max(worst, abs(g - fd) / gscale)
+    assert worst <= 2.0 ** -70, worst
