@@ -96,9 +96,12 @@ static_assert(chunks_per_fold<2>() == 4 && chunks_per_fold<3>() == 2 && chunks_p
 constexpr int NB_MAX = KC / 2; // complex panel width per chunk
 constexpr int BM = 128;        // tile rows (TMEM lanes)
 constexpr int NST = 4;         // A pipeline stages
+constexpr int NSB = 2;         // B buffers (one K chunk's slices each)
+// warp 0: A producer, warp 1: TMEM owner and MMA issuer, warp 2: B producer,
+// then EW epilogue warps
 template <int L>
 constexpr int threads_of() {
-  return 32 * (2 + Cfg<L>::EW);
+  return 32 * (3 + Cfg<L>::EW);
 }
 constexpr int TMEM_COLS = 512;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bound on every wait
@@ -666,8 +669,10 @@ __device__ __forceinline__ bool fold_diagonals(uint32_t (&F)[NH][Cfg<L>::FW], ui
 
 // C (m x n complex) = C - A B (BETA) or A B, from the slices of A (rows) and
 // B (columns) cut by k_oz_split_a / k_oz_split_b.  Persistent: one CTA per SM
-// walks the (row tile, column tile) grid.  Warp 0 lane 0: TMA producer.
-// Warp 1: TMEM owner and MMA issuer (lane 0).  Warps 2 .. 1+EW: epilogue.
+// walks the (row tile, column tile) grid.  Warp 0 lane 0: TMA producer of
+// the A slices (NST-stage ring).  Warp 1: TMEM owner and MMA issuer (lane 0).
+// Warp 2 lane 0: TMA producer of the B slices (NSB chunk buffers, so the next
+// chunk loads during the current one's MMAs).  Warps 3 .. 2+EW: epilogue.
 template <int L, bool BETA>
 __global__ void __launch_bounds__(threads_of<L>(), 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, View C, int64_t m,
@@ -683,10 +688,10 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
   constexpr int NH = N / NPART;          // columns per epilogue thread
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *sB = base;
-  uint8_t *sA = base + B_BYTES;
+  uint8_t *sB = base;                  // NSB buffers of B_BYTES
+  uint8_t *sA = base + NSB * B_BYTES;
   __shared__ __align__(8) uint64_t bar_afull[NST], bar_aempty[NST];
-  __shared__ __align__(8) uint64_t bar_bfull, bar_bempty, bar_accempty;
+  __shared__ __align__(8) uint64_t bar_bfull[NSB], bar_bempty[NSB], bar_accempty;
   constexpr int NGRP = (S + CF::GS - 1) / CF::GS;  // fold groups of diagonals
   __shared__ __align__(8) uint64_t bar_grp[NGRP];
   __shared__ uint32_t s_tmem;
@@ -697,8 +702,10 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
       mbar_init(&bar_afull[i], 1);
       mbar_init(&bar_aempty[i], 1);
     }
-    mbar_init(&bar_bfull, 1);
-    mbar_init(&bar_bempty, 1);
+    for (int i = 0; i < NSB; i++) {
+      mbar_init(&bar_bfull[i], 1);
+      mbar_init(&bar_bempty[i], 1);
+    }
     for (int i = 0; i < NGRP; i++) mbar_init(&bar_grp[i], 1);
     mbar_init(&bar_accempty, EPI_WARPS);
     s_err = 0;
@@ -714,19 +721,37 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
   const uint32_t tmem = s_tmem;
   const int64_t mt = (m + BM - 1) / BM, nt = Npad / N, total = mt * nt;
 
-  if (warp == 0) {
-    if (lane == 0) {  // ---------------------------------------- producer
-      uint32_t a_it = 0, r = 0;
+  if (warp == 2) {
+    if (lane == 0) {  // -------------------------------------- B producer
+      // the Se B slices of each K chunk into one of NSB buffers: the next
+      // chunk's slices load while the MMAs of the current chunk run
+      uint32_t r = 0;
       for (int64_t t = blockIdx.x; t < total && !s_err; t += gridDim.x) {
-        const int mtile = (int)(t / nt), ntile = (int)(t % nt);
+        const int ntile = (int)(t % nt);
         for (int c = 0; c < nchunks; c++, r++) {
-          if (!mbar_wait(&bar_bempty, (r & 1) ^ 1)) {
+          const int b = (int)(r % NSB);
+          if (!mbar_wait(&bar_bempty[b], ((r / NSB) & 1) ^ 1)) {
             s_err = 1;
             break;
           }
-          mbar_expect_tx(&bar_bfull, (uint32_t)(Se * B_TILE));
+          mbar_expect_tx(&bar_bfull[b], (uint32_t)(Se * B_TILE));
           for (int q = 0; q < Se; q++)
-            tma_load_2d(sB + q * B_TILE, &tmB, &bar_bfull, 0, (c * S + q) * Npad + ntile * N);
+            tma_load_2d(sB + b * B_BYTES + q * B_TILE, &tmB, &bar_bfull[b], 0, (c * S + q) * Npad + ntile * N);
+        }
+      }
+      // drain: wait for the last loads of every buffer to land before leaving
+      for (int i = 0; i < NSB && r > 0; i++) {
+        const uint32_t it = r - 1 - i;
+        if ((int)it < 0) break;
+        mbar_wait(&bar_bfull[it % NSB], (it / NSB) & 1);
+      }
+    }
+  } else if (warp == 0) {
+    if (lane == 0) {  // -------------------------------------- A producer
+      uint32_t a_it = 0;
+      for (int64_t t = blockIdx.x; t < total && !s_err; t += gridDim.x) {
+        const int mtile = (int)(t / nt);
+        for (int c = 0; c < nchunks; c++) {
           for (int p = 0; p < Se; p++, a_it++) {
             const int st = a_it % NST;
             const uint32_t ph = (a_it / NST) & 1;
@@ -746,7 +771,6 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
         if ((int)it < 0) break;
         mbar_wait(&bar_afull[it % NST], (it / NST) & 1);
       }
-      if (r > 0) mbar_wait(&bar_bfull, (r - 1) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // --------------------------------------------- MMA
@@ -757,7 +781,8 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
           // overwrites the diagonals once the epilogue has read the previous
           // group, its last chunk signals the diagonal groups
           const bool gfirst = c % CPF == 0, glast = c % CPF == CPF - 1 || c == nchunks - 1;
-          if ((gfirst && !mbar_wait(&bar_accempty, (g & 1) ^ 1)) || !mbar_wait(&bar_bfull, r & 1)) {
+          const int b = (int)(r % NSB);
+          if ((gfirst && !mbar_wait(&bar_accempty, (g & 1) ^ 1)) || !mbar_wait(&bar_bfull[b], (r / NSB) & 1)) {
             s_err = 3;
             break;
           }
@@ -778,7 +803,7 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
             const int ncols = (Se - p) * N;
             for (int c0 = 0; c0 < ncols; c0 += 256) {
               const int nn = min(256, ncols - c0);
-              const uint32_t b0 = smem_u32(sB) + (uint32_t)(c0 * KC * 2);
+              const uint32_t b0 = smem_u32(sB + b * B_BYTES) + (uint32_t)(c0 * KC * 2);
               const uint32_t d = tmem + (uint32_t)(p * N + c0);
               const uint32_t idesc = umma_idesc_n(nn);
 #pragma unroll
@@ -792,15 +817,16 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
             if (glast && ((p + 1) % CF::GS == 0 || p == Se - 1)) umma_commit(&bar_grp[p / CF::GS]);
           }
           if (s_err) break;
-          umma_commit(&bar_bempty);
+          umma_commit(&bar_bempty[b]);
           if (glast) g++;
         }
       }
     }
   } else {  // ---------------------------------------------------- epilogue
-    const int quarter = warp & 3, half = (warp - 2) >> 2;  // half: column part 0 .. NPART-1
+    // TMEM lanes [32 (warp % 4), + 32) are the ones a warp may access
+    const int quarter = warp & 3, half = (warp - 3) >> 2;  // half: column part 0 .. NPART-1
     const int row = quarter * 32 + lane;
-    const int etid = threadIdx.x - 64;  // 0 .. 32 * EPI_WARPS - 1
+    const int etid = threadIdx.x - 96;  // 0 .. 32 * EPI_WARPS - 1
     const Scratch sc{reinterpret_cast<uint32_t *>(sA + NST * A_BYTES) + etid, EPI_WARPS * 32};
     const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * NH);
     uint32_t g = 0;  // fold groups
@@ -984,7 +1010,8 @@ int gemm(bool beta, View A, View B, View C, int64_t m, int64_t n, int64_t k, voi
   constexpr int SCR_BYTES = (2 * Cfg<L>::RW + 2) * Cfg<L>::EW * 32 * 4;  // epilogue scratch
   constexpr int THREADS = threads_of<L>();
   // at least ~116 KB so that a single CTA (and its 512 TMEM columns) fits per SM
-  const int smem = std::max(B_BYTES + NST * A_BYTES + SCR_BYTES + 1024, 116 * 1024);
+  const int smem = std::max(NSB * B_BYTES + NST * A_BYTES + SCR_BYTES + 1024, 116 * 1024);
+  static_assert(NSB * B_BYTES + NST * A_BYTES + SCR_BYTES + 1024 <= 227 * 1024, "shared memory of k_oz_gemm");
   const int64_t tiles = ((m + BM - 1) / BM) * (z.Npad / Cfg<L>::N);
   const int grid = (int)std::min<int64_t>(tiles, sm_count());
   if (beta) {
