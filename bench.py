@@ -65,11 +65,11 @@ OZAKI_S = {"dd": 16, "td": 24, "qd": 32}
 # the n = 4096 DD step: n2 = 3968 rows and columns, K = 256 realified).  It is
 # reported, scaled to the average trailing launch by n2^2, only while the
 # kernel source is the one it was taken on (sha1 of csrc/ozaki.cuh).
-OZ_TRAFFIC = {"dd": {"bytes": 971030272 + 477952256, "n2": 3968, "src_sha1": "cb83ea875dc66ff7beee53aa17073ebe7a24110c"}}
+OZ_TRAFFIC = {"dd": {"bytes": 606346752 + 468483840, "n2": 3968, "src_sha1": "4b50dafc85d50e75ec2fff17acf26f58e2302925"}}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one cooperative panel
 # launch (the first 32-column sub-panel of n = 2048: m = 2048 rows), valid
 # while the kernel's source is unchanged
-PANEL_TRAFFIC = {"dd": {"bytes": 2218240 + 36608, "m": 2048, "w": 32, "src_sha1": "a8c5c09c55acb7e3f14cec7d491797c84913a32f"}}
+PANEL_TRAFFIC = {"dd": {"bytes": 2237440 + 14592, "m": 2048, "w": 32, "src_sha1": "d6fc05caa117742aeae43b56a1a6d89c5c052c59"}}
 # unit roundoff exponents: u = 2^-104 / 2^-157 / 2^-209
 U_EXP = {"dd": 104, "td": 157, "qd": 209}
 
@@ -115,7 +115,32 @@ def parse():
     p.add_argument("--sweep", action="store_true",
                    help="block-width sweep instead of the benchmark line: LU + solve GFLOP/s for every method "
                         "and nb at --n (default 1024), plus the unblocked form; one JSON line per point")
+    p.add_argument("--profile-step", action="store_true",
+                   help="one untimed LU + solve of the workload (after one at n = 256) and nothing else: "
+                        "the command that launch lists and ncu captures run")
     return p.parse_args()
+
+
+def run_profile_step(args):
+    """One factorisation + solve of the configured workload, untimed, after
+    the same at n = 256 (kernels loaded, workspace pool warm), with no probe,
+    clock sampler or oracle: a short, fixed launch sequence for profilers."""
+    import torch
+    from paper_2403_16013_gb300 import api, build, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    L = LIMBS[args.prec]
+    nb = args.nb if args.nb else (128 if args.method == "ozaki" else 64)
+    for n in (256, args.n):
+        A = torch.from_numpy(inputs.gaussian_matrix(n, L, seed=1)).cuda()
+        b = torch.from_numpy(inputs.complex_gaussian_vector(n, L, seed=2)).cuda()
+        LU, ipiv, info = api.lu_factor(A, method=args.method, nb=nb, ozaki_slices=args.slices,
+                                       sub_nb=args.sub_nb)
+        api.lu_solve(LU, ipiv, b)
+        torch.cuda.synchronize()
+        if int(info.item()) != 0:
+            raise SystemExit(f"profile step: info = {int(info.item())} at n = {n}")
+    print(f"profile step ok: {args.prec} {args.method} n={args.n} nb={nb}", flush=True)
 
 
 def dist_init():
@@ -626,6 +651,9 @@ def main():
         return
     if args.zgemm:
         run_zgemm(args)
+        return
+    if args.profile_step:
+        run_profile_step(args)
         return
     import torch
 

@@ -719,6 +719,10 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
+  // Tiles in column-major order: consecutive CTAs take the row tiles of one
+  // column tile, so a wave reads a few B tiles and all of A (a few tens of
+  // MB at n = 4096), which stay in L2; in row-major order each B tile came
+  // back only after a whole row of tiles and was read again from DRAM.
   const int64_t mt = (m + BM - 1) / BM, nt = Npad / N, total = mt * nt;
 
   if (warp == 2) {
@@ -727,7 +731,7 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
       // chunk's slices load while the MMAs of the current chunk run
       uint32_t r = 0;
       for (int64_t t = blockIdx.x; t < total && !s_err; t += gridDim.x) {
-        const int ntile = (int)(t % nt);
+        const int ntile = (int)(t / mt);  // column-major tile order (see above)
         for (int c = 0; c < nchunks; c++, r++) {
           const int b = (int)(r % NSB);
           if (!mbar_wait(&bar_bempty[b], ((r / NSB) & 1) ^ 1)) {
@@ -750,7 +754,7 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
     if (lane == 0) {  // -------------------------------------- A producer
       uint32_t a_it = 0;
       for (int64_t t = blockIdx.x; t < total && !s_err; t += gridDim.x) {
-        const int mtile = (int)(t / nt);
+        const int mtile = (int)(t % mt);
         for (int c = 0; c < nchunks; c++) {
           for (int p = 0; p < Se; p++, a_it++) {
             const int st = a_it % NST;
@@ -832,7 +836,7 @@ __global__ void __launch_bounds__(threads_of<L>(), 1)
     uint32_t g = 0;  // fold groups
     const int ngroups = (nchunks + CPF - 1) / CPF;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-      const int mtile = (int)(t / nt), ntile = (int)(t % nt);
+      const int mtile = (int)(t % mt), ntile = (int)(t / mt);
       uint32_t F[NH][FW];
 #pragma unroll
       for (int cc = 0; cc < NH; cc++)
