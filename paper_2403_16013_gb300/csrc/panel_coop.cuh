@@ -7,17 +7,19 @@
 // global-memory traffic except the pivot exchange.  Per column j:
 //   1. every CTA picks its candidate among its rows i >= j (column j is up
 //      to date) by the leading-limb key k0 (full cabs1 keys only where two
-//      k0 are near) and writes (k0, row) to its key slot with a release
-//      stamp (the column), the candidate's full key with a second stamp;
+//      k0 are near) and writes (k0, row) to its key slot as two
+//      self-validating words that carry the column (no fence), the
+//      candidate's full key under a release stamp;
 //   2. it then applies the pending rank-1 update of column j-1 to the
 //      columns after j (one step of lookahead: only column j was updated
 //      before the keys), first to its best row and to row j, which it
 //      publishes (all nb columns) together with the reciprocal of its best
 //      value under a release flag stamped with the column, then to its other
 //      rows;
-//   3. meanwhile one warp reads every CTA's key slot (bounded waits on the
-//      stamps; same winner p everywhere, ties to the lowest row; the full keys
-//      are read only for slots whose k0 are near the largest), waits for
+//   3. meanwhile one warp reads every CTA's key slot (bounded polling until
+//      both words carry the column; integer comparisons only; same winner p
+//      everywhere, ties to the lowest row; the full keys are read only for
+//      slots whose k0 are near the largest), waits for
 //      the winner's flag, stages its row and swaps rows j and p where this
 //      CTA owns them (both were published rows, so the update of step 2
 //      never touches them);
@@ -44,7 +46,7 @@ constexpr int COOP_KS = 16;                     // doubles per key slot (one 128
 
 struct CoopWS {
   int *status;    // nonzero: a wait timed out
-  double *kslot;  // [2][G][COOP_KS] by column parity: full key, row + stamp 1, stamp 2, k0 (slot_ints)
+  double *kslot;  // [2][G][COOP_KS] by column parity: header words, full key, stamp 2 (see the key slot below)
   double *prow;   // [2][G][nb][2L] best row of each CTA, by column parity
   double *srow;   // [2][nb][2L] row j, by column parity
   int *rcp_flag;  // [2G] column stamp (j + 1) of the reciprocal and rows of each slot
@@ -58,12 +60,6 @@ __device__ __forceinline__ void named_sync(int id, int count) {
 // Arrive at that barrier without waiting (the producers of a bar.sync).
 __device__ __forceinline__ void named_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ int ld_relaxed(const int *p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
 }
 
 // Bounded wait until *flag == v; false on timeout.
@@ -103,39 +99,72 @@ __device__ __forceinline__ bool key_near(double k0, double kmax) {
   return order_key(kmax) - order_key(k0) <= KEY_NEAR_ULPS;
 }
 
-// Key slot of one CTA for one column parity (COOP_KS doubles): the full key
-// in doubles 0 .. L-1; the row and stamp 1 in double L (two ints); stamp 2 in
-// double L+1; k0 in double L+2.  Stamp 1 (column + 1) releases k0 and the
-// row, stamp 2 the full key.  The full key of a candidate picked by k0 alone
-// is computed off the critical path and may follow later; it is read only
-// when another CTA's k0 is near.
-template <int L>
-__device__ __forceinline__ int *slot_ints(double *slot) {
-  return reinterpret_cast<int *>(slot + L);
+// Key slot of one CTA for one column parity (COOP_KS doubles = one 128-byte
+// line).  The common path is two 64-bit words, each of which validates
+// itself, so a reader needs neither a fence nor a second round trip:
+//   word 0: the column stamp (j + 1) in the high 32 bits, the candidate row
+//           in bits 0..30 (INT_MAX: no candidate), bit 31 set when k0 is
+//           exactly zero;
+//   word 1: the bits of k0 (-1.0: no candidate) with the low KEY_STAMP_BITS
+//           mantissa bits replaced by the low bits of the stamp.
+// A 64-bit aligned access is single-copy atomic, so a word that shows this
+// column's stamp holds this column's value (word 0 is still stored with
+// release and the reader fences once after its polling: that orders each
+// CTA's reads of the pivot rows of column j before its stamp of column j+1,
+// which the owner of those row buffers awaits before it rewrites them); stale words hold an earlier
+// column (the stamp bits of word 1 repeat only after 2^20 columns, far
+// beyond any order that fits in memory).  Truncating k0 to its high bits is
+// monotone, so the truncated keys order the candidates except within
+// KEY_SLOT_NEAR of each other, where the full keys decide.  Those follow in
+// doubles 2 .. L+1 under stamp 2 (an int in double L+2, released).
+constexpr int KEY_STAMP_BITS = 20;
+constexpr unsigned long long KEY_STAMP_MASK = (1ull << KEY_STAMP_BITS) - 1;
+// |exact key - k0| < 2^-51 k0 and the truncation removes less than 2^-32 k0,
+// so truncated keys further apart than 2^-30.9 (relative) are ordered as the
+// exact keys; 2^23 units of the order key is 2^-30 or more.
+constexpr long long KEY_SLOT_NEAR = 1ll << 23;
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 
-// Publication of this CTA's candidate (one thread): k0 and the row under
-// stamp 1; with has_key, the full key under stamp 2 as well.
+template <int L>
+__device__ __forceinline__ int *slot_stamp2(double *slot) {
+  return reinterpret_cast<int *>(slot + L + 2);
+}
+
+// Publication of this CTA's candidate (one thread): the two header words;
+// with has_key, the full key under stamp 2 as well.
 template <int L>
 __device__ __forceinline__ void publish_key_slot(double *slot, int64_t j, int cand, double k0, bool has_key,
                                                  const double *key) {
-  int *si = slot_ints<L>(slot);
-  slot[L + 2] = k0;
-  si[0] = cand;
+  const unsigned long long stamp = (unsigned long long)(j + 1);
   if (has_key) {
 #pragma unroll
-    for (int l = 0; l < L; l++) slot[l] = key[l];
+    for (int l = 0; l < L; l++) slot[2 + l] = key[l];
+    st_release(slot_stamp2<L>(slot), (int)(j + 1));
   }
-  st_release(si + 1, (int)(j + 1));
-  if (has_key) st_release(si + 2, (int)(j + 1));
+  const unsigned long long kb = (unsigned long long)__double_as_longlong(k0);
+  const unsigned zero = kb == 0 ? 0x80000000u : 0u;
+  unsigned long long *w = reinterpret_cast<unsigned long long *>(slot);
+  st_relaxed_u64(w + 1, (kb & ~KEY_STAMP_MASK) | (stamp & KEY_STAMP_MASK));
+  st_release_u64(w, (stamp << 32) | (unsigned)((unsigned)cand & 0x7fffffffu) | zero);
 }
 
 // The full key of a candidate chosen by k0 alone, published under stamp 2.
 template <int L>
 __device__ __forceinline__ void publish_full_key(double *slot, int64_t j, const R<L> &key) {
 #pragma unroll
-  for (int l = 0; l < L; l++) slot[l] = key.x[l];
-  st_release(slot_ints<L>(slot) + 2, (int)(j + 1));
+  for (int l = 0; l < L; l++) slot[2 + l] = key.x[l];
+  st_release(slot_stamp2<L>(slot), (int)(j + 1));
 }
 
 struct Winner {
@@ -146,84 +175,92 @@ struct Winner {
 };
 
 // The pivot of column j over all G key slots of parity par, run by one warp:
-// lane l takes slots l, l + 32, ...; their stamps 1 are read together
-// (relaxed) until all carry the column, then one fence orders the reads of
-// k0 and rows after them (an acquire pattern).  The largest k0 (ties: the
-// lowest row) wins unless another slot's k0 is near it; then the full keys of
-// the near slots are awaited (stamp 2, acquire) and compared.
+// lane l takes slots l, l + 32, ...; it polls both header words of each
+// until they carry the column (bounded), keeping the values it validated.
+// The largest truncated k0 (ties: the lowest row) wins unless another slot's
+// truncated k0 is within KEY_SLOT_NEAR; then the full keys of the near slots
+// are awaited (stamp 2, acquire) and compared.  Integer operations only,
+// except on that rare path.
 template <int L>
 __device__ Winner exchange_winner(const CoopWS &cw, int par, int G, int64_t j, int lane) {
   constexpr int KMAX = COOP_GMAX / 32;
-  const int stamp = (int)(j + 1);
+  const unsigned long long stamp = (unsigned long long)(j + 1);
+  long long keys[KMAX];  // truncated k0 bits (negative: no candidate)
+  int rows[KMAX];
+  unsigned zflag = 0;    // slots whose k0 is exactly zero
   unsigned pendk = 0;
 #pragma unroll
-  for (int k = 0; k < KMAX; k++)
+  for (int k = 0; k < KMAX; k++) {
+    keys[k] = LLONG_MIN;
+    rows[k] = INT_MAX;
     if (lane + 32 * k < G) pendk |= 1u << k;
+  }
   bool ok = true;
   const long long t0 = clock64();
   while (pendk) {
-    unsigned still = 0;
 #pragma unroll
     for (int k = 0; k < KMAX; k++)
       if ((pendk >> k) & 1u) {
-        double *slot = cw.kslot + ((size_t)par * G + lane + 32 * k) * COOP_KS;
-        if (ld_relaxed(slot_ints<L>(slot) + 1) != stamp) still |= 1u << k;
+        const unsigned long long *w =
+            reinterpret_cast<const unsigned long long *>(cw.kslot + ((size_t)par * G + lane + 32 * k) * COOP_KS);
+        const unsigned long long w0 = ld_relaxed_u64(w), w1 = ld_relaxed_u64(w + 1);
+        if ((w0 >> 32) == stamp && (w1 & KEY_STAMP_MASK) == (stamp & KEY_STAMP_MASK)) {
+          keys[k] = (long long)(w1 & ~KEY_STAMP_MASK);
+          rows[k] = (int)(w0 & 0x7fffffffu);
+          if (w0 & 0x80000000u) zflag |= 1u << k;
+          pendk &= ~(1u << k);
+        }
       }
-    pendk = still;
     if (pendk && clock64() - t0 > COOP_WAIT) {
       ok = false;
       break;
     }
   }
-  __threadfence();
-  double k0s[KMAX];
-  int rows[KMAX];
-  R<1> bk = invalid_key<1>();
-  int bi = INT_MAX, bq = -1;
-#pragma unroll
-  for (int k = 0; k < KMAX; k++) {
-    k0s[k] = -1.0;
-    rows[k] = INT_MAX;
-    if (ok && lane + 32 * k < G) {
-      double *slot = cw.kslot + ((size_t)par * G + lane + 32 * k) * COOP_KS;
-      k0s[k] = __ldcg(slot + L + 2);
-      rows[k] = __ldcg(slot_ints<L>(slot));
-      R<1> kk;
-      kk.x[0] = k0s[k];
-      if (better<1>(kk, rows[k], bk, bi)) {
-        bk = kk;
-        bi = rows[k];
-        bq = par * G + lane + 32 * k;
-      }
-    }
-  }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
   Winner res{j, -1, true, __all_sync(0xffffffffu, ok)};
   if (!res.ok) return res;
-  int my = bi, myq = bq;
-  warp_argmax<1>(bk, bi);
+  // this lane's best slot, then the warp's: largest key, then lowest row
+  long long bk = LLONG_MIN;
+  int bi = INT_MAX, bq = -1;
+  bool bz = false;
+#pragma unroll
+  for (int k = 0; k < KMAX; k++)
+    if (rows[k] != INT_MAX && (keys[k] > bk || (keys[k] == bk && rows[k] < bi))) {
+      bk = keys[k];
+      bi = rows[k];
+      bq = par * G + lane + 32 * k;
+      bz = (zflag >> k) & 1u;
+    }
+  const unsigned long long u = (unsigned long long)bk ^ 0x8000000000000000ull;
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, (unsigned)(u >> 32));
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, (unsigned)(u >> 32) == mhi ? (unsigned)u : 0u);
+  const bool top = (unsigned)(u >> 32) == mhi && (unsigned)u == mlo;
+  const int wrow = (int)__reduce_min_sync(0xffffffffu, top ? (unsigned)bi : 0xffffffffu);
+  const long long kmax = (long long)((((unsigned long long)mhi << 32) | mlo) ^ 0x8000000000000000ull);
   bool nearx = false;
-  if (bk.x[0] >= 0.0) {
+  if (kmax >= 0) {
 #pragma unroll
     for (int k = 0; k < KMAX; k++)
-      if (k0s[k] >= 0.0 && rows[k] != bi && key_near(k0s[k], bk.x[0])) nearx = true;
+      if (rows[k] != INT_MAX && keys[k] >= 0 && rows[k] != wrow && kmax - keys[k] <= KEY_SLOT_NEAR) nearx = true;
   }
-  bool zero = !(bk.x[0] > 0.0);
+  int my = top && bi == wrow ? bi : INT_MAX, myq = bq;
+  bool zero = kmax < 0 || __any_sync(0xffffffffu, top && bi == wrow && bz);
+  int win = wrow;
   if (__any_sync(0xffffffffu, nearx)) {
-    // full keys of the slots within the window of the largest k0
-    const double kmax = bk.x[0];
+    // full keys of the slots within the window of the largest truncated k0
     R<L> fk = invalid_key<L>();
     int fi = INT_MAX, fq = -1;
 #pragma unroll
     for (int k = 0; k < KMAX; k++) {
-      if (!ok || k0s[k] < 0.0 || !key_near(k0s[k], kmax)) continue;
+      if (rows[k] == INT_MAX || keys[k] < 0 || kmax - keys[k] > KEY_SLOT_NEAR) continue;
       double *slot = cw.kslot + ((size_t)par * G + lane + 32 * k) * COOP_KS;
-      if (!coop_wait_flag(slot_ints<L>(slot) + 2, stamp)) {
+      if (!coop_wait_flag(slot_stamp2<L>(slot), (int)stamp)) {
         ok = false;
         continue;
       }
       R<L> kk;
 #pragma unroll
-      for (int l = 0; l < L; l++) kk.x[l] = __ldcg(slot + l);
+      for (int l = 0; l < L; l++) kk.x[l] = __ldcg(slot + 2 + l);
       if (better<L>(kk, rows[k], fk, fi)) {
         fk = kk;
         fi = rows[k];
@@ -235,13 +272,13 @@ __device__ Winner exchange_winner(const CoopWS &cw, int par, int G, int64_t j, i
     my = fi;
     myq = fq;
     warp_argmax<L>(fk, fi);
-    bi = fi;
+    win = fi;
     zero = !(fk.x[0] > 0.0);
   }
-  const unsigned own = __ballot_sync(0xffffffffu, my == bi && my != INT_MAX);
+  const unsigned own = __ballot_sync(0xffffffffu, my == win && my != INT_MAX);
   res.part = own ? __shfl_sync(0xffffffffu, myq, __ffs(own) - 1) : -1;
   res.zero = zero;
-  res.p = (bi == INT_MAX || zero) ? j : bi;
+  res.p = (win == INT_MAX || zero) ? j : win;
   return res;
 }
 
