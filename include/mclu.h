@@ -249,8 +249,10 @@ int zozaki_split_qd(int side, int64_t rows, int64_t cols, const double *X, int64
  *            0 add, 1 sub, 2 mul, 3 div
  *          complex ops on plane arrays [2][L][count]:
  *            10 add, 11 sub, 12 mul (4M, Eq. 1), 13 mul (3M, Eq. 2),
- *            14 div, 15 inv (reciprocal), 16 cabs1 (result in the real part)
- *   x, y   device inputs (y ignored by 15, 16); z device output
+ *            14 div, 15 inv (reciprocal), 16 cabs1 (result in the real part),
+ *            17 inv by Newton's method from a binary64 seed (the panel's
+ *            pivot reciprocal)
+ *   x, y   device inputs (y ignored by 15, 16, 17); z device output
  */
 int mclu_vec_op(int op, int L, int64_t count, const double *x, const double *y, double *z, void *stream);
 

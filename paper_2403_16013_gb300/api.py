@@ -131,7 +131,7 @@ def adjoint_rank1(lam: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
 
 
 _VEC_OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "cadd": 10, "csub": 11, "cmul": 12, "cmul3m": 13,
-            "cdiv": 14, "cinv": 15, "cabs1": 16}
+            "cdiv": 14, "cinv": 15, "cabs1": 16, "cinv_newton": 17}
 
 
 def vec_op(op: str, x: torch.Tensor, y: torch.Tensor | None = None, z: torch.Tensor | None = None) -> torch.Tensor:

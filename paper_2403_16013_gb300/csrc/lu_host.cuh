@@ -153,15 +153,25 @@ int launch_tri_block(dim3 grid, dim3 block, cudaStream_t s, View A, int64_t k0, 
 // chain is latency bound (bs <= 64, or TD/QD up to 128: measured faster),
 // else the one-thread-per-row block solve (DD at 128 rows is bound by each
 // SMSP's FP64 throughput, where the extra barriers cost more).
+// With ncols2 > 0 the same triangle also solves columns 0 .. ncols2-1 of X2
+// (rows xrow2 ..), in the same launch where the four-warp-group kernel runs.
 template <int L>
-int launch_lsolve(cudaStream_t s, View A, int64_t k0, int bs, View X, int64_t ncols, int64_t xrow0) {
-  if (ncols <= 0) return 0;
+int launch_lsolve(cudaStream_t s, View A, int64_t k0, int bs, View X, int64_t ncols, int64_t xrow0,
+                  View X2 = View{nullptr, 0, 0}, int64_t ncols2 = 0, int64_t xrow2 = 0) {
+  if (ncols < 0 || ncols2 < 0) return (int)cudaErrorInvalidValue;
+  if (ncols + ncols2 == 0) return 0;
   const int RT = (bs + 31) / 32 * 32;
   if (bs <= 64 || (L >= 3 && bs <= 128)) {
-    k_lsolve4<L><<<(unsigned)ncols, dim3(RT, 4), lsolve4_smem<L>(RT), s>>>(A, k0, bs, X, xrow0, 0);
+    k_lsolve4<L><<<(unsigned)(ncols + ncols2), dim3(RT, 4), lsolve4_smem<L>(RT), s>>>(A, k0, bs, X, xrow0, 0, X2,
+                                                                                      ncols, xrow2);
     MCLU_LAUNCHED();
     return 0;
   }
+  if (ncols2 > 0) {
+    int rc = launch_lsolve<L>(s, A, k0, bs, X2, ncols2, xrow2);
+    if (rc) return rc;
+  }
+  if (ncols == 0) return 0;
   // one column per CTA: the solve is bound by each SM's FP64 unit, so the
   // columns go to as many SMs as possible
   return launch_tri_block<L, true, true, false>(dim3((unsigned)ncols), dim3(RT, 1), s, A, k0, bs, X, ncols, nullptr, 0,
@@ -390,7 +400,8 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   Workspace w;
   const size_t oz_need = ozk ? oz::ws_bytes<L>(n, n, nb) : 0;
   const size_t ws_need = getrf_ws_bytes<L>(n, nb, m3) + oz_need +
-                         (ozk ? (((size_t)2 * 2 * L * nb * nb * sizeof(double) + 255) & ~(size_t)255) : 0);
+                         (ozk ? (((size_t)(L == 2 ? 1 : 2) * 2 * L * nb * nb * sizeof(double) + 255) & ~(size_t)255)
+                              : 0);
   char *ws_base = nullptr;
   if (ext_ws) {
     if (ext_bytes < ws_need) return MCLU_ERR_SCRATCH_CAPACITY;
@@ -425,7 +436,9 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     sumU = cv.take<double>((size_t)n * nb * L);
   }
   void *oz_ws = ozk ? (void *)cv.take<char>(oz_need) : nullptr;
-  double *winv = ozk ? cv.take<double>((size_t)2 * 2 * L * nb * nb) : nullptr;  // L11^-1 and a scratch block
+  // L11^-1 of the current block; for TD / QD also the scratch of its composition
+  double *winv = ozk ? cv.take<double>((size_t)(L == 2 ? 1 : 2) * 2 * L * nb * nb) : nullptr;
+  double *oz_tmp = winv + (size_t)2 * L * nb * nb;
   int *oz_status = ws.zflag + 1;  // spare word of the header block
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
   MCLU_TRY(cudaMemsetAsync(cw.rcp_flag, 0, (size_t)2 * COOP_GMAX * sizeof(int), s));
@@ -476,20 +489,46 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
       // their U rows by the block solve, an Ozaki product for the rest), so
       // that the trailing update below takes all jb columns in one product
       // (K = 2 jb realified: several TMEM chunks, one exact C - P per element).
+      //
+      // When a trailing part follows, W = L11^{-1} is formed on the way, one
+      // row block per sub-panel R_s: once R_s is factored and its swaps are
+      // applied, its rows of L11 are final, and
+      //   W[R_s, 0..s0) = -L11[R_s, ..s0) W[..s0, ..s0)   (an Ozaki product)
+      //   W[R_s, 0..send) = L_ss^{-1} W[R_s, 0..send)     (W starts as I)
+      // the solve sharing the launch of the block solve for the U rows.
+      // (DD only: with the 16-column sub-panels of TD and QD the eight row
+      // blocks cost more than the composition below; measured at n = 4096:
+      // TRSM 21.1 -> 24.1 ms (TD), 30.3 -> 33.2 ms (QD), DD 12.6 -> 10.1 ms)
+      const bool mkw = jend < n && L == 2;
+      View Wb{winv, jb, jb * jb};
+      if (mkw) {
+        k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(Wb, jb);
+        MCLU_LAUNCHED();
+      }
       for (int64_t s0 = j0; s0 < jend; s0 += sbw) {
         const int64_t send = std::min<int64_t>(s0 + sbw, jend), sb = send - s0;
         int rc = panel(s0, send);
         if (rc) return rc;
         rc = laswp(s0, send, j0, jend, s0, send);  // the block's other columns, in one launch
         if (rc) return rc;
+        if (mkw && s0 > j0) {
+          ProfScope ps(PK_TRSM, s);
+          rc = oz::gemm<L>(true, View{Ap + j0 * lda + s0, lda, lda * n}, Wb, View{winv + (s0 - j0), jb, jb * jb}, sb,
+                           s0 - j0, s0 - j0, oz_ws, oz_status, s, note_launch, Se);
+          if (rc) return rc;
+        }
         if (send < jend) {
           ProfScope ps(PK_OTHER, s);
           View U{Ap + send * lda, lda, lda * n};  // rows s0.., columns send..jend
-          rc = launch_lsolve<L>(s, A, s0, (int)sb, U, jend - send, s0);
+          rc = launch_lsolve<L>(s, A, s0, (int)sb, U, jend - send, s0, Wb, mkw ? send - j0 : 0, s0 - j0);
           if (rc) return rc;
           rc = oz::gemm<L>(true, View{Ap + s0 * lda + send, lda, lda * n}, View{Ap + send * lda + s0, lda, lda * n},
                            View{Ap + send * lda + send, lda, lda * n}, n - send, jend - send, sb, oz_ws, oz_status, s,
                            note_launch, Se);
+          if (rc) return rc;
+        } else if (mkw) {
+          ProfScope ps(PK_TRSM, s);
+          rc = launch_lsolve<L>(s, A, s0, (int)sb, Wb, send - j0, s0 - j0);
           if (rc) return rc;
         }
       }
@@ -507,39 +546,39 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
           int rc = launch_lsolve<L>(s, A, j0, (int)jb, A12, n2, j0);
           if (rc) return rc;
         } else {
-          // W = L11^{-1} (unit lower, jb x jb) by the same block solve on the
-          // identity, then U12 = W A12 as an Ozaki product written in place
-          // (the operands are sliced before the product is stored).
+          // U12 = W A12 with W = L11^{-1} (DD: formed with the sub-panels
+          // above), as an Ozaki product written in place (the operands are
+          // sliced before the product is stored).
           View W{winv, jb, jb * jb};
-          k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(W, jb);
-          MCLU_LAUNCHED();
-          constexpr int SB = oz::NB_MAX;  // 32: the sub-panel width
-          if (jb <= SB || (L == 2 && jb <= 128)) {
-            // one CTA per column of W (the solve is FP64-latency bound, so
-            // the jb columns go to jb SMs); for DD blocks up to 128 this
-            // direct solve measured faster than the composition below (its
-            // FP64 chain is short)
-            int rc0 = launch_lsolve<L>(s, A, j0, (int)jb, W, jb, 0);
-            if (rc0) return rc0;
-          } else {
-            // the inverses of the 32 x 32 diagonal blocks in one launch, then
-            // 2 x 2 block inversion upwards: inv([[P, 0], [C, Q]]) has the
+          if (L != 2) {
+            // W by the block solve on the identity (one 32-column sub-panel),
+            // else the inverses of the 32 x 32 diagonal blocks in one launch
+            // and 2 x 2 block inversion upwards: inv([[P, 0], [C, Q]]) has the
             // lower-left block -inv(Q) C inv(P), two Ozaki products per pair
-            const int nsb = (int)cdiv(jb, SB);
-            k_lsolve4<L><<<dim3(SB, nsb), dim3(SB, 4), lsolve4_smem<L>(SB), s>>>(A, j0, (int)jb, W, 0, SB);
+            k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(W, jb);
             MCLU_LAUNCHED();
-            View Tm{winv + (size_t)2 * L * nb * nb, nb, (int64_t)nb * nb};  // scratch for C inv(P)
-            for (int64_t h = SB; h < jb; h *= 2) {
-              for (int64_t a = 0; a + h < jb; a += 2 * h) {
-                const int64_t hb = std::min<int64_t>(h, jb - a - h);  // rows of Q
-                View Cv{Ap + (j0 + a) * lda + (j0 + a + h), lda, lda * n};  // L rows a+h.., columns a..
-                View Pi{W.p + a * W.ld + a, W.ld, W.ps};
-                View Qi{W.p + (a + h) * W.ld + (a + h), W.ld, W.ps};
-                View X21{W.p + a * W.ld + (a + h), W.ld, W.ps};
-                int rc1 = oz::gemm<L>(false, Cv, Pi, Tm, hb, h, h, oz_ws, oz_status, s, note_launch, Se);
-                if (rc1) return rc1;
-                rc1 = oz::gemm<L>(true, Qi, Tm, X21, hb, h, hb, oz_ws, oz_status, s, note_launch, Se);
-                if (rc1) return rc1;
+            constexpr int SB = oz::NB_MAX;  // 32
+            if (jb <= SB) {
+              int rc0 = launch_lsolve<L>(s, A, j0, (int)jb, W, jb, 0);
+              if (rc0) return rc0;
+            } else {
+              const int nsb = (int)cdiv(jb, SB);
+              k_lsolve4<L><<<dim3(SB, nsb), dim3(SB, 4), lsolve4_smem<L>(SB), s>>>(A, j0, (int)jb, W, 0, SB,
+                                                                                   View{nullptr, 0, 0}, INT64_MAX, 0);
+              MCLU_LAUNCHED();
+              View Tm{oz_tmp, nb, (int64_t)nb * nb};  // scratch for C inv(P)
+              for (int64_t h = SB; h < jb; h *= 2) {
+                for (int64_t a = 0; a + h < jb; a += 2 * h) {
+                  const int64_t hb = std::min<int64_t>(h, jb - a - h);  // rows of Q
+                  View Cv{Ap + (j0 + a) * lda + (j0 + a + h), lda, lda * n};  // L rows a+h.., columns a..
+                  View Pi{W.p + a * W.ld + a, W.ld, W.ps};
+                  View Qi{W.p + (a + h) * W.ld + (a + h), W.ld, W.ps};
+                  View X21{W.p + a * W.ld + (a + h), W.ld, W.ps};
+                  int rc1 = oz::gemm<L>(false, Cv, Pi, Tm, hb, h, h, oz_ws, oz_status, s, note_launch, Se);
+                  if (rc1) return rc1;
+                  rc1 = oz::gemm<L>(true, Qi, Tm, X21, hb, h, hb, oz_ws, oz_status, s, note_launch, Se);
+                  if (rc1) return rc1;
+                }
               }
             }
           }
@@ -891,12 +930,12 @@ int ozaki_split(int side, int64_t rows, int64_t cols, const double *X, int64_t l
 template <int L>
 int vec_op(int op, int64_t count, const double *x, const double *y, double *z, cudaStream_t s) {
   const bool real = op >= 0 && op <= 3;
-  const bool cplx = op >= 10 && op <= 16;
+  const bool cplx = op >= 10 && op <= 17;
   if (!real && !cplx) return -1;
   if (count < 0) return -3;
   if (count == 0) return 0;
   if (!x) return -4;
-  if (!y && op != 15 && op != 16) return -5;
+  if (!y && op < 15) return -5;
   if (!z) return -6;
   k_vec_op<L><<<(unsigned)cdiv(count, 128), 128, 0, s>>>(op, count, x, y, z);
   MCLU_LAUNCHED();

@@ -636,17 +636,26 @@ __global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, c
 //   p = 2: Im x - sum Re T Im x     p = 3: - sum Im T Re x
 // so each step costs every SMSP one product (the four warp groups run on
 // four FP64 units), and x_k = (P0 + P1) + i (P2 + P3) is formed when row k
-// is final.  Column k of T is streamed into shared memory one step ahead
-// (double-buffered).  Block (bs rounded up to 32, 4), bs <= 128.
+// is final.  Column k of T is streamed through registers and shared memory
+// ahead of its step (below).  Block (bs rounded up to 32, 4), bs <= 128.
 // ystep > 0: the grid's y index selects the diagonal block at offset
 // y ystep of a bs-row block (its rows, its columns of X), bs <= ystep rows
 // each: the diagonal-block inverses of a larger triangle in one launch.
+// Columns blockIdx.x >= ncol1 are columns blockIdx.x - ncol1 of a second
+// right-hand side X2 (rows xrow2 ..): two solves with the same triangle in
+// one launch.
 template <int L>
-__global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, View X, int64_t xrow0, int ystep) {
+__global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, View X, int64_t xrow0, int ystep,
+                                                 View X2, int64_t ncol1, int64_t xrow2) {
   const int r = threadIdx.x, p = threadIdx.y;
   const int RT = blockDim.x;
   const int tid = p * RT + r, nthr = 4 * RT;
   int64_t c = blockIdx.x;
+  if (c >= ncol1) {
+    X = X2;
+    c -= ncol1;
+    xrow0 = xrow2;
+  }
   if (ystep > 0) {
     const int koff = (int)blockIdx.y * ystep;
     bs = min(ystep, bs - koff);
@@ -656,9 +665,9 @@ __global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, Vie
     c += koff;
   }
   extern __shared__ double lsm4[];
-  double *col = lsm4;                              // [2][RT][2L]: column k of T
-  double *part = col + (size_t)2 * RT * 2 * L;     // [4][L]: row k's partial accumulators
-  double *xk = part + 4 * L;                       // [2L]: x_k
+  double *col = lsm4;                              // [3][RT][2L]: column k of T
+  double *part = col + (size_t)3 * RT * 2 * L;     // [2][4][L]: row k's partial accumulators
+  double *xk = part + 2 * 4 * L;                   // [2][2L]: x_k
   const bool own = r < bs;
   Acc<L> acc;
   acc.zero();
@@ -666,64 +675,74 @@ __global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, Vie
     const Z<L> x = ldz<L>(X, xrow0 + r, c);
     acc.set(p == 0 ? x.re : x.im);
   }
-  auto fetch = [&](int k, int buf) {  // column k of T, rows k+1 .. bs-1
-    for (int t = tid; t < bs; t += nthr) {
-      if (t <= k) continue;
-      const Z<L> v = ldz<L>(A, k0 + t, k0 + k);
-      double *d = col + ((size_t)buf * RT + t) * 2 * L;
+  // Column k of T (rows k+1 .. bs-1, one row per thread) is loaded into
+  // registers during step k-2 and stored to shared memory during step k-1,
+  // so no step waits for a global load.  Columns, partial accumulators and
+  // x_k rotate through buffers (3, 2, 2), which leaves two barriers a step.
+  const bool frow = tid < bs;
+  Z<L> pre;
+  auto load_col = [&](int k) {
+    if (frow && k < bs && tid > k) pre = ldz<L>(A, k0 + tid, k0 + k);
+  };
+  auto store_col = [&](int k) {
+    if (frow && k < bs && tid > k) {
+      double *d = col + ((size_t)(k % 3) * RT + tid) * 2 * L;
 #pragma unroll
       for (int q = 0; q < L; q++) {
-        d[q] = v.re.x[q];
-        d[L + q] = v.im.x[q];
+        d[q] = pre.re.x[q];
+        d[L + q] = pre.im.x[q];
       }
     }
   };
-  fetch(0, 0);
+  load_col(0);
+  store_col(0);
+  load_col(1);
   __syncthreads();
   for (int k = 0; k < bs; k++) {
-    const int buf = k & 1;
-    if (k + 1 < bs) fetch(k + 1, buf ^ 1);
+    const int par = k & 1;
+    store_col(k + 1);
+    load_col(k + 2);
     if (r == k) {
 #pragma unroll
-      for (int q = 0; q < L; q++) part[p * L + q] = acc.s[q];
+      for (int q = 0; q < L; q++) part[(par * 4 + p) * L + q] = acc.s[q];
     }
     __syncthreads();
     if (r == 0 && (p == 0 || p == 2)) {  // x_k: Re on (0,0), Im on (0,2)
       Acc<L> t, o;
 #pragma unroll
       for (int q = 0; q < L; q++) {
-        t.s[q] = part[p * L + q];
-        o.s[q] = part[(p + 1) * L + q];
+        t.s[q] = part[(par * 4 + p) * L + q];
+        o.s[q] = part[(par * 4 + p + 1) * L + q];
       }
       t.add_acc(o, false);
       const R<L> v = t.result();
 #pragma unroll
       for (int q = 0; q < L; q++) {
-        xk[(p >> 1) * L + q] = v.x[q];
+        xk[par * 2 * L + (p >> 1) * L + q] = v.x[q];
         X.p[(int64_t)((p >> 1) * L + q) * X.ps + c * X.ld + xrow0 + k] = v.x[q];
       }
     }
     __syncthreads();
     if (own && r > k) {
-      const double *d = col + ((size_t)buf * RT + r) * 2 * L;
+      const double *d = col + ((size_t)(k % 3) * RT + r) * 2 * L;
+      const double *xv_ = xk + par * 2 * L;
       R<L> tv, xv;
 #pragma unroll
       for (int q = 0; q < L; q++) {
         tv.x[q] = d[(p == 0 || p == 2) ? q : L + q];    // Re T for p = 0, 2; Im T for p = 1, 3
-        xv.x[q] = xk[(p == 0 || p == 1) ? (p == 0 ? q : L + q) : (p == 2 ? L + q : q)];
+        xv.x[q] = xv_[(p == 0 || p == 1) ? (p == 0 ? q : L + q) : (p == 2 ? L + q : q)];
       }
       if (p == 1)
         acc.template add_prod<false>(tv, xv);
       else
         acc.template add_prod<true>(tv, xv);
     }
-    __syncthreads();
   }
 }
 
 template <int L>
 constexpr size_t lsolve4_smem(int RT) {
-  return ((size_t)2 * RT * 2 * L + 4 * L + 2 * L) * sizeof(double);
+  return ((size_t)3 * RT * 2 * L + 2 * 4 * L + 2 * 2 * L) * sizeof(double);
 }
 
 // Shared memory of k_tri_block for block size bs and CT columns.
@@ -1540,7 +1559,7 @@ __global__ void k_vec_op(int op, int64_t count, const double *x, const double *y
   View vy{const_cast<double *>(y), count, count};
   View vz{z, count, count};
   Z<L> a = ldz<L>(vx, e, 0), b, r;
-  if (op != 15 && op != 16) b = ldz<L>(vy, e, 0);
+  if (op < 15) b = ldz<L>(vy, e, 0);
   switch (op) {
     case 10: r = z_add<L>(a, b); break;
     case 11: r = z_sub<L>(a, b); break;
@@ -1548,6 +1567,7 @@ __global__ void k_vec_op(int op, int64_t count, const double *x, const double *y
     case 13: r = z_mul3m<L>(a, b); break;
     case 14: r = z_div<L>(a, b); break;
     case 15: r = z_inv<L>(a); break;
+    case 17: r = z_inv_newton<L>(a); break;
     default:
       r.re = z_abs1<L>(a);
       r.im = r_zero<L>();

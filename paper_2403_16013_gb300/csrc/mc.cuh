@@ -503,6 +503,115 @@ __device__ __forceinline__ Z<L> z_inv(const Z<L> &a) {
   return r;
 }
 
+// 1/p by Newton's method from a binary64 seed: a shorter chain of FP64
+// instructions than conj(p)/|p|^2 with a multi-component reciprocal (the
+// pivot reciprocal of the panel, which every column waits for).
+//   seed   r0 = conj(p0) RN(1/RN(|p0|^2)), p0 = a0 + b0 i the leading limbs:
+//          relative error a few units of 2^-53;
+//   resid  e = 1 - p r0, of order 2^-52.  Its leading terms cancel:
+//          a0 Re r0 and -b0 Im r0 lie in [0, 1] and add up to about 1, so
+//          1 minus the larger one is split exactly into a rounded value and
+//          its error (Fast2Sum), and the rounded value nearly cancels the
+//          smaller one; a0 Im r0 and b0 Re r0 are nearly opposite, so their
+//          sum is exact.  The TwoProd and Fast2Sum errors and the products
+//          with the lower limbs are added in binary64: absolute error about
+//          2^-105;
+//   finish r = r0 (1 + e + e^2) (1/p = r0 / (1 - e)), the correction in
+//          binary64 and added to r0 with TwoSum: relative error of order
+//          |e|^3 + 2^-105.
+// The real and imaginary parts of e and of r are independent chains (the
+// panel runs them on two SMSPs).  L >= 3 adds one Newton step
+// r <- r + r (1 - p r) in L-limb arithmetic.
+struct RcpSeed {
+  double rr, ri;  // Re r0, Im r0
+};
+
+__device__ __forceinline__ RcpSeed rcp_seed(double a0, double b0) {
+  const double d = __fma_rn(a0, a0, __dmul_rn(b0, b0));
+  const double q = __drcp_rn(d);
+  return {__dmul_rn(a0, q), flip(__dmul_rn(b0, q))};
+}
+
+// Re e = 1 - (a Re r0 - b Im r0)
+template <int L>
+__device__ __forceinline__ double rcp_resid_re(const R<L> &a, const R<L> &b, const RcpSeed &s) {
+  double p1, e1, p2, e2;
+  two_prod(a.x[0], s.rr, p1, e1);  // p1 >= 0
+  two_prod(b.x[0], s.ri, p2, e2);  // p2 <= 0
+  // the larger of p1 and -p2 (integer compare of nonnegative doubles) is
+  // subtracted from 1 first, its rounding error kept (Fast2Sum: 1 is not
+  // smaller in magnitude); the result then nearly cancels the other product
+  const bool big1 = __double_as_longlong(p1) >= __double_as_longlong(flip(p2));
+  const double c = big1 ? __dsub_rn(1.0, p1) : __dadd_rn(1.0, p2);
+  const double cl = big1 ? __dsub_rn(__dsub_rn(1.0, c), p1) : __dadd_rn(__dsub_rn(1.0, c), p2);
+  const double s0 = big1 ? __dadd_rn(c, p2) : __dsub_rn(c, p1);
+  double t = __dadd_rn(__dsub_rn(e2, e1), cl);
+  t = __fma_rn(flip(a.x[1]), s.rr, t);
+  t = __fma_rn(b.x[1], s.ri, t);
+  return __dadd_rn(s0, t);
+}
+
+// Im e = -(a Im r0 + b Re r0)
+template <int L>
+__device__ __forceinline__ double rcp_resid_im(const R<L> &a, const R<L> &b, const RcpSeed &s) {
+  double q1, f1, q2, f2;
+  two_prod(a.x[0], s.ri, q1, f1);
+  two_prod(b.x[0], s.rr, q2, f2);
+  const double s0 = __dadd_rn(q1, q2);  // exact: q1 and q2 are nearly opposite
+  double t = __dadd_rn(f1, f2);
+  t = __fma_rn(a.x[1], s.ri, t);
+  t = __fma_rn(b.x[1], s.rr, t);
+  return flip(__dadd_rn(s0, t));
+}
+
+// One part of r0 (1 + e + e^2): IM = false the real part, true the imaginary
+// part, as a two-limb value (limbs 2 .. L-1 zero).
+template <int L, bool IM>
+__device__ __forceinline__ R<L> rcp_finish(const RcpSeed &s, double er, double ei) {
+  // u = e + e^2
+  const double ur = __dadd_rn(er, __fma_rn(er, er, flip(__dmul_rn(ei, ei))));
+  const double ui = __fma_rn(__dadd_rn(er, er), ei, ei);
+  // delta = r0 u
+  const double d = IM ? __fma_rn(s.rr, ui, __dmul_rn(s.ri, ur)) : __fma_rn(s.rr, ur, flip(__dmul_rn(s.ri, ui)));
+  R<L> r = r_zero<L>();
+  two_sum(IM ? s.ri : s.rr, d, r.x[0], r.x[1]);
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ Z<L> z_inv_newton(const Z<L> &p) {
+  const RcpSeed s = rcp_seed(p.re.x[0], p.im.x[0]);
+  const double er = rcp_resid_re<L>(p.re, p.im, s);
+  const double ei = rcp_resid_im<L>(p.re, p.im, s);
+  Z<L> r;
+  r.re = rcp_finish<L, false>(s, er, ei);
+  r.im = rcp_finish<L, true>(s, er, ei);
+  if constexpr (L >= 3) {
+    // e = 1 - p r, then r + r e, in L-limb arithmetic
+    Acc<L> t;
+    t.zero();
+    t.s[0] = 1.0;
+    t.template add_prod<true>(p.re, r.re);
+    t.template add_prod<false>(p.im, r.im);
+    const R<L> e_re = t.result();
+    t.zero();
+    t.template add_prod<true>(p.re, r.im);
+    t.template add_prod<true>(p.im, r.re);
+    const R<L> e_im = t.result();
+    Acc<L> u;
+    u.set(r.re);
+    u.template add_prod<false>(r.re, e_re);
+    u.template add_prod<true>(r.im, e_im);
+    const R<L> n_re = u.result();
+    u.set(r.im);
+    u.template add_prod<false>(r.re, e_im);
+    u.template add_prod<false>(r.im, e_re);
+    r.im = u.result();
+    r.re = n_re;
+  }
+  return r;
+}
+
 // a / b = a conj(b) / |b|^2 with both real parts divided by long division
 template <int L>
 __device__ __forceinline__ Z<L> z_div(const Z<L> &a, const Z<L> &b) {

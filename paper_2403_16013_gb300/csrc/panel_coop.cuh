@@ -423,10 +423,10 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     const bool has = cand != INT_MAX;                                // uniform over the CTA
     const int cr = has ? (int)(cand - rbeg) : -1;                    // local row of the candidate
     const int jr = (j >= rbeg && j < rend) ? (int)(j - rbeg) : -1;  // local row j
-    // 2. warps 0 and 1: the reciprocal 1/p = conj(p) / |p|^2 of the
-    //    candidate (SMSPs 0 and 1: Re p^2 and Im p^2 in parallel, the real
-    //    reciprocal x of |p|^2 on warp 0, then Re p x and -Im p x in
-    //    parallel; warps 4 and 5 keep off those two FP64 units meanwhile);
+    // 2. warps 0 and 1: the reciprocal 1/p of the candidate by Newton's
+    //    method from a binary64 seed (z_inv_newton: the real and imaginary
+    //    parts of the residual and of the result on SMSPs 0 and 1; warps 4
+    //    and 5 keep off those two FP64 units meanwhile);
     //    warps 2 and 7: the pending update of the candidate row and of row j,
     //    published to their slots; once all four are done thread 0 releases
     //    the flag.  Warp 3 publishes the key and does step 3 at the same time
@@ -434,41 +434,30 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     //    update goes in 32-element pieces to whole warps: 6 at once, the
     //    others when free.
     if ((w & 2) == 0) {
-      __shared__ double s_inv[2 * L];  // Im p^2 accumulator, then x
+      __shared__ double s_e[2];  // Re e, Im e of the Newton step
       const bool act = has && lane == 0 && w < 2;
       Z<L> pv;
-      Acc<L> t;
+      RcpSeed sd;
       if (act) {
         pv = ldp(cr, jc);
-        const R<L> h = w == 0 ? pv.re : pv.im;
-        t.set_prod(h, h);
-        if (w == 1) {
-#pragma unroll
-          for (int l = 0; l < L; l++) s_inv[l] = t.s[l];
-        }
+        sd = rcp_seed(pv.re.x[0], pv.im.x[0]);
+        s_e[w] = w == 0 ? rcp_resid_re<L>(pv.re, pv.im, sd) : rcp_resid_im<L>(pv.re, pv.im, sd);
       }
-      named_sync(1, 128);
-      if (has && tid == 0) {
-        Acc<L> o;
-#pragma unroll
-        for (int l = 0; l < L; l++) o.s[l] = s_inv[l];
-        t.add_acc(o, false);
-        const R<L> x = r_recip<L>(t.result());
-#pragma unroll
-        for (int l = 0; l < L; l++) s_inv[L + l] = x.x[l];
-      }
-      if (w == 5 && lane == 0 && has && fast)  // SMSP 1 is free while thread 0 runs the chain
-        publish_full_key<L>(cw.kslot + (size_t)q * COOP_KS, j, pivot_key<L>(ldp(cr, jc)));
       named_sync(1, 128);
       if (act) {
-        R<L> x;
-#pragma unroll
-        for (int l = 0; l < L; l++) x.x[l] = s_inv[L + l];
-        R<L> v = r_mul<L>(w == 0 ? pv.re : pv.im, x);
-        if (w == 1) v = r_neg<L>(v);
+        R<L> v;
+        if constexpr (L == 2) {
+          v = w == 0 ? rcp_finish<L, false>(sd, s_e[0], s_e[1]) : rcp_finish<L, true>(sd, s_e[0], s_e[1]);
+        } else {  // (the team kernel factors TD and QD panels)
+          const Z<L> z = z_inv_newton<L>(pv);
+          v = w == 0 ? z.re : z.im;
+        }
 #pragma unroll
         for (int l = 0; l < L; l++) ws.part_rcp[(int64_t)q * 2 * L + w * L + l] = v.x[l];
       }
+      named_sync(1, 128);
+      if (w == 5 && lane == 0 && has && fast)  // off the reciprocal's SMSPs' critical window
+        publish_full_key<L>(cw.kslot + (size_t)q * COOP_KS, j, pivot_key<L>(ldp(cr, jc)));
     } else if (w == 2 || w == 7) {
       // warp 2: the candidate row (and the row-j slot when it is row j);
       // warp 7: row j when it is another row of this CTA
@@ -499,11 +488,11 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         }
       }
       named_arrive(3, 96);  // rows cr and jr are final: warp 3 may swap them
+      if (w == 2) named_arrive(4, 64);  // warp 6 may take SMSP 2's FP64 unit
     }
     if (w == 0 || w == 1 || w == 2 || w == 7) {
       named_sync(2, 128);
       if (has && tid == 0) {
-        __threadfence();
         st_release(cw.rcp_flag + q, (int)(j + 1));
       }
     }
@@ -551,7 +540,12 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
           if (zero && *ws.info == 0) *ws.info = (int)(j + 1);
         }
       }
-    } else if (pend) {
+    } else {
+      // warp 6 shares SMSP 2 with warp 2: it starts its share of the pending
+      // update once the candidate row (on the path to the flag) is done
+      if (w == 6) named_sync(4, 64);
+    }
+    if (w != 3 && pend) {
       const int rlo = (int)max((int64_t)0, j - rbeg);  // rows i > j - 1
       const int nrow = nr - rlo, ncol = nb - jc - 1;
       const int tot = nrow > 0 ? nrow * ncol : 0;

@@ -52,22 +52,55 @@ def test_real_ops(api, orc, L, op):
 
 
 @pytest.mark.parametrize("L", [2, 3, 4])
-@pytest.mark.parametrize("op", ["cmul", "cmul3m", "cdiv", "cinv", "cabs1", "cadd"])
+@pytest.mark.parametrize("op", ["cmul", "cmul3m", "cdiv", "cinv", "cinv_newton", "cabs1", "cadd"])
 def test_complex_ops(api, orc, L, op):
     rng = np.random.default_rng(600 + L)
     N = 8000
     x = np.stack([rand_limbs(L, N, rng, -8, 8), rand_limbs(L, N, rng, -8, 8)])
     y = np.stack([rand_limbs(L, N, rng, -8, 8), rand_limbs(L, N, rng, -8, 8)])
-    one_arg = op in ("cinv", "cabs1")
+    one_arg = op in ("cinv", "cinv_newton", "cabs1")
     g = host(api.vec_op(op, dev(x), None if one_arg else dev(y)))
     code = {"cmul": orc.COP_MUL4M, "cmul3m": orc.COP_MUL3M, "cdiv": orc.COP_DIV, "cinv": orc.COP_INV,
-            "cabs1": orc.COP_ABS1, "cadd": orc.COP_ADD}[op]
-    o = orc.cplx_op(code, y if op == "cinv" else x, None if one_arg else y) if op != "cinv" else orc.cplx_op(code, x)
+            "cinv_newton": orc.COP_INV, "cabs1": orc.COP_ABS1, "cadd": orc.COP_ADD}[op]
+    o = orc.cplx_op(code, x) if one_arg else orc.cplx_op(code, x, y)
     ax = np.abs(x[:, 0]).sum(axis=0)
     ay = np.abs(y[:, 0]).sum(axis=0)
     scale = {"cmul": ax * ay, "cmul3m": ax * ay, "cdiv": ax / np.hypot(y[0, 0], y[1, 0]),
-             "cinv": 1 / np.hypot(x[0, 0], x[1, 0]), "cabs1": ax, "cadd": ax + ay}[op]
+             "cinv": 1 / np.hypot(x[0, 0], x[1, 0]), "cinv_newton": 1 / np.hypot(x[0, 0], x[1, 0]),
+             "cabs1": ax, "cadd": ax + ay}[op]
     err = np.maximum(np.abs(exact_diff(orc, g[0], o[0])), np.abs(exact_diff(orc, g[1], o[1])))
     ratio = err / (2.0 ** (-53 * L) * scale)
     worst = int(np.argmax(ratio))
     assert ratio[worst] <= 256, (op, L, worst, ratio[worst])
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_inv_newton_edges(api, orc, L):
+    """The pivot reciprocal by Newton's method from a binary64 seed (op 17) on
+    the cases its exact cancellations rest on: purely real and purely
+    imaginary values (one leading product zero), |Re| and |Im| far apart in
+    either order, equal or nearly equal (both leading products near 1/2, where
+    1 minus either is inexact), and exponents over 2^+-400 -- within the same
+    256 u_L of 1/|x| as the multi-component reciprocal, against the oracle."""
+    rng = np.random.default_rng(700 + L)
+    N = 4000
+    x = np.stack([rand_limbs(L, N, rng, -8, 8), rand_limbs(L, N, rng, -8, 8)])
+    q = N // 8
+    x[1, :, :q] = 0.0                                   # real
+    x[0, :, q:2 * q] = 0.0                              # imaginary
+    x[1, :, 2 * q:3 * q] *= 2.0 ** -40                  # |Re| >> |Im|
+    x[0, :, 3 * q:4 * q] *= 2.0 ** -40                  # |Im| >> |Re|
+    x[1, :, 4 * q:5 * q] = x[0, :, 4 * q:5 * q]         # Re = Im
+    x[:, :, 5 * q:6 * q] *= 2.0 ** 400
+    x[:, :, 6 * q:7 * q] *= 2.0 ** -400
+    x[1, 0, 7 * q:] = x[0, 0, 7 * q:] * (1 + 2.0 ** -40)  # Re and Im a few units apart
+    x[1, 1:, 7 * q:] = x[0, 1:, 7 * q:]
+    g = host(api.vec_op("cinv_newton", dev(x)))
+    o = orc.cplx_op(orc.COP_INV, x)
+    err = np.maximum(np.abs(exact_diff(orc, g[0], o[0])), np.abs(exact_diff(orc, g[1], o[1])))
+    ratio = err / (2.0 ** (-53 * L) / np.hypot(x[0, 0], x[1, 0]))
+    worst = int(np.argmax(ratio))
+    assert ratio[worst] <= 256, (L, worst, ratio[worst], x[:, :, worst])
+    for j in range(0, N, 61):
+        for c in range(2):
+            assert is_nonoverlapping(list(g[c, :, j]), strict=False)
