@@ -350,22 +350,17 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
   }
   __shared__ int s_zero, s_next, s_pend, s_ok, s_cand, s_fast;
   __shared__ double s_rcp[2 * L], s_key[L], s_k0;
-  if (tid == 0) {
-    s_next = 0;
-    s_pend = 0;
-    s_ok = 1;
-  }
-  __syncthreads();
-  for (int jc = 0; jc < nb; jc++) {
-    const int64_t j = j0 + jc;
-    const int par = jc & 1;
-    double *su = su2 + (size_t)par * RW;                 // pivot row of column jc
-    const double *sprev = su2 + (size_t)(par ^ 1) * RW;  // pivot row of column jc - 1
-    const bool pend = s_pend != 0;  // the update of columns jc+1.. from column jc-1 is pending
-    const int q = par * G + b;
-    // 1. the CTA's candidate among its rows i >= j: the largest k0 (one FP64
-    //    addition per row), unless another row's k0 is near it; then the
-    //    full keys of the near rows decide (s_fast = 0, s_key the full key)
+  // The CTA's candidate for panel column c among its rows i >= jrow: the
+  // largest k0 (one FP64 addition per row), unless another row's k0 is near
+  // it; then the full keys of the near rows decide (s_fast = 0, s_key the
+  // full key).  s_k0 is the largest k0 either way.
+  //   select_block: all threads (barriers inside);
+  //   select_warp0: warp 0 alone when the CTA has at most 32 rows (one row a
+  //   lane, warp shuffles only): run at the end of the previous column, right
+  //   after warps 0 and 1 have formed column c, it saves the column start
+  //   four block barriers.
+  const bool fused = rpc <= 32;
+  auto select_block = [&](int jc, int64_t j) {
     {
       R<1> k1 = invalid_key<1>();
       int idx = INT_MAX;
@@ -418,6 +413,50 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       }
       __syncthreads();
     }
+  };
+  auto select_warp0 = [&](int c, int64_t jrow) {
+    const int64_t i = rbeg + lane;
+    const bool act = lane < nr && i >= jrow;
+    R<1> k;
+    k.x[0] = act ? cheap_key<L>(sp, c, rpc, lane) : -1.0;
+    R<1> kk = k;
+    int ii = act ? (int)i : INT_MAX;
+    warp_argmax<1>(kk, ii);
+    const bool nearl = act && ii != INT_MAX && key_near(k.x[0], kk.x[0]);  // the winner included
+    if (__any_sync(0xffffffffu, nearl && (int)i != ii)) {
+      R<L> fk = nearl ? pivot_key<L>(ldp(lane, c)) : invalid_key<L>();
+      int fi = nearl ? (int)i : INT_MAX;
+      warp_argmax<L>(fk, fi);
+      if (lane == 0) {
+#pragma unroll
+        for (int l = 0; l < L; l++) s_key[l] = fk.x[l];
+        s_cand = fi;
+        s_k0 = kk.x[0];
+        s_fast = 0;
+      }
+    } else if (lane == 0) {
+      s_cand = ii;
+      s_k0 = kk.x[0];
+      s_fast = 1;
+    }
+  };
+  if (tid == 0) {
+    s_next = 0;
+    s_pend = 0;
+    s_ok = 1;
+  }
+  if (fused && w == 0) select_warp0(0, j0);
+  __syncthreads();
+  for (int jc = 0; jc < nb; jc++) {
+    const int64_t j = j0 + jc;
+    const int par = jc & 1;
+    double *su = su2 + (size_t)par * RW;                 // pivot row of column jc
+    const double *sprev = su2 + (size_t)(par ^ 1) * RW;  // pivot row of column jc - 1
+    const bool pend = s_pend != 0;  // the update of columns jc+1.. from column jc-1 is pending
+    const int q = par * G + b;
+    // 1. the CTA's candidate among its rows i >= j (with at most 32 rows a
+    //    CTA, warp 0 chose it at the end of the previous column)
+    if (!fused) select_block(jc, j);
     const int cand = s_cand;
     const bool fast = s_fast != 0;
     const bool has = cand != INT_MAX;                                // uniform over the CTA
@@ -577,6 +616,10 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
           z.im = im.result();
           stp(rr, jc + 1, z);
         }
+        if (fused) {
+          __syncthreads();
+          if (w == 0) select_warp0(jc + 1, j + 1);
+        }
       }
       if (tid == 0) {
         s_pend = 0;
@@ -662,6 +705,10 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
             double *d = sp + (size_t)cc * 2 * L * rpc + rr + (size_t)(w * L) * rpc;
 #pragma unroll
             for (int l = 0; l < L; l++) d[(size_t)l * rpc] = v.x[l];
+          }
+          if (fused) {  // column cc is final on warps 0 and 1: the next candidate
+            named_sync(5, 64);
+            if (w == 0) select_warp0(cc, j + 1);
           }
         }
       }
