@@ -272,26 +272,9 @@ __device__ __forceinline__ void add_shifted(uint32_t (&acc)[W], uint64_t mant, i
 
 // --------------------------------------------------------------- split --
 
-// Power-of-two scales.  rows = true: Ea_i over row i of the m x k block X
-// (both parts, all columns); rows = false: Eb_j over column j of the k x n
-// block.  E = max floor(log2 |leading limb|) + 2, so |x| < 2^(E-1).
-template <int L>
-__global__ void k_oz_scales(View X, int64_t count, int64_t len, bool rows, int *E) {
-  const int lane = threadIdx.x & 31;
-  const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // one warp per row / column
-  if (v >= count) return;
-  int e = -100000;
-  for (int64_t t = lane; t < len; t += 32) {
-    const int64_t i = rows ? v : t, j = rows ? t : v;
-    const int64_t o = j * X.ld + i;
-    const double re = X.p[o], im = X.p[(int64_t)L * X.ps + o];
-    if (!is_zero(re)) e = max(e, ilogb_bits(re));
-    if (!is_zero(im)) e = max(e, ilogb_bits(im));
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
-  if (lane == 0) E[v] = (e == -100000) ? 0 : e + 2;
-}
+// Power-of-two scales: Ea_i over row i of the m x k block A (both parts, all
+// columns), Eb_j over column j of the k x n block B.  E = max floor(log2
+// |leading limb|) + 2, so |x| < 2^(E-1).
 
 // Balanced base-2^BETA digits of x / 2^E (S digits, most significant first).
 template <int L>
@@ -333,65 +316,78 @@ __device__ __forceinline__ void digits_of(const double (&x)[L], int E, float (&d
   }
 }
 
-// A side: row i of the m x k block (k <= 32 per chunk), chunk c = blockIdx.y.
-// Output slices [chunk][S][Mpad][64] bf16: columns 0..31 hold Re, 32..63 Im.
-template <int L>
-__global__ void k_oz_split_a(View X, int64_t m, int64_t k, const int *Ea, __nv_bfloat16 *out, int64_t Mpad, int Se) {
-  constexpr int S = Cfg<L>::S;
-  const int lane = threadIdx.x & 31;
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int c = blockIdx.y;
-  if (i >= Mpad) return;
-  const int64_t col = (int64_t)c * NB_MAX + lane;
-  const bool ok = i < m && col < k;
-  const int E = ok ? Ea[i] : 0;
-#pragma unroll
-  for (int part = 0; part < 2; part++) {
-    double x[L];
-#pragma unroll
-    for (int l = 0; l < L; l++) x[l] = ok ? X.p[(int64_t)(part * L + l) * X.ps + col * X.ld + i] : 0.0;
-    float dg[S];
-    digits_of<L>(x, E, dg);
-    __nv_bfloat16 *o = out + (((int64_t)c * S) * Mpad + i) * KC + part * NB_MAX + lane;
-#pragma unroll
-    for (int p = 0; p < S; p++)
-      if (p < Se) o[(int64_t)p * Mpad * KC] = __float2bfloat16_rn(dg[p]);
-  }
-}
+// Slice layout.  A: [chunk][S][Mpad][64] bf16 for 32 complex columns per
+// chunk: columns 0..31 hold Re, 32..63 Im.  B: [chunk][S][Npad][64] with
+// Npad >= 2n: row 2j = [Re B_.j ; -Im B_.j], row 2j+1 = [Im B_.j ; Re B_.j]
+// (K index: 0..31 first half, 32..63 second).
 
-// B side: column j of the k x n block, chunk c = blockIdx.y.  Output slices
-// [chunk][S][Npad][64] with Npad >= 2n: row 2j = [Re B_.j ; -Im B_.j],
-// row 2j+1 = [Im B_.j ; Re B_.j] (K index: 0..31 first half, 32..63 second).
+// Scales and slices of both operands in one launch: warp v < Mpad takes row
+// v of A (its scale Ea over the whole row, then its slices chunk by chunk,
+// one column a lane), warp Mpad + j column j of B (Eb, then its slices, one
+// row a lane).  Padding rows and columns get zero slices and scale 0.
 template <int L>
-__global__ void k_oz_split_b(View X, int64_t k, int64_t n, const int *Eb, __nv_bfloat16 *out, int64_t Npad, int Se) {
+__global__ void k_oz_split_ab(View A, View B, int64_t m, int64_t n, int64_t k, int *Ea, int *Eb,
+                              __nv_bfloat16 *as, __nv_bfloat16 *bs, int64_t Mpad, int64_t Npad, int nchunks, int Se) {
   constexpr int S = Cfg<L>::S;
   const int lane = threadIdx.x & 31;
-  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int c = blockIdx.y;
-  if (2 * j >= Npad) return;
-  const int64_t row = (int64_t)c * NB_MAX + lane;
-  const bool ok = j < n && row < k;
-  const int E = ok ? Eb[j] : 0;
-  float dre[S], dim[S];
-  {
-    double x[L];
-#pragma unroll
-    for (int l = 0; l < L; l++) x[l] = ok ? X.p[(int64_t)l * X.ps + j * X.ld + row] : 0.0;
-    digits_of<L>(x, E, dre);
-#pragma unroll
-    for (int l = 0; l < L; l++) x[l] = ok ? X.p[(int64_t)(L + l) * X.ps + j * X.ld + row] : 0.0;
-    digits_of<L>(x, E, dim);
+  const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const bool aside = v < Mpad;
+  const int64_t idx = aside ? v : v - Mpad;  // row of A or column of B
+  if (!aside && 2 * idx >= Npad) return;
+  const View X = aside ? A : B;
+  const bool real = aside ? idx < m : idx < n;
+  // element t of this row (A) or column (B)
+  auto off = [&](int64_t t) -> int64_t { return aside ? t * X.ld + idx : idx * X.ld + t; };
+  int e = -100000;
+  if (real) {
+    for (int64_t t = lane; t < k; t += 32) {
+      const int64_t o = off(t);
+      const double re = X.p[o], im = X.p[(int64_t)L * X.ps + o];
+      if (!is_zero(re)) e = max(e, ilogb_bits(re));
+      if (!is_zero(im)) e = max(e, ilogb_bits(im));
+    }
   }
-  __nv_bfloat16 *o0 = out + (((int64_t)c * S) * Npad + 2 * j) * KC;
-  __nv_bfloat16 *o1 = o0 + KC;
 #pragma unroll
-  for (int q = 0; q < S; q++) {
-    if (q >= Se) break;
-    const int64_t so = (int64_t)q * Npad * KC;
-    o0[so + lane] = __float2bfloat16_rn(dre[q]);
-    o0[so + NB_MAX + lane] = __float2bfloat16_rn(-dim[q]);
-    o1[so + lane] = __float2bfloat16_rn(dim[q]);
-    o1[so + NB_MAX + lane] = __float2bfloat16_rn(dre[q]);
+  for (int d = 16; d > 0; d >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, d));
+  const int E = (e == -100000) ? 0 : e + 2;
+  if (lane == 0) (aside ? Ea : Eb)[idx] = E;
+  for (int c = 0; c < nchunks; c++) {
+    const int64_t t = (int64_t)c * NB_MAX + lane;
+    const bool ok = real && t < k;
+    if (aside) {
+#pragma unroll
+      for (int part = 0; part < 2; part++) {
+        double x[L];
+#pragma unroll
+        for (int l = 0; l < L; l++) x[l] = ok ? X.p[(int64_t)(part * L + l) * X.ps + off(t)] : 0.0;
+        float dg[S];
+        digits_of<L>(x, E, dg);
+        __nv_bfloat16 *o = as + (((int64_t)c * S) * Mpad + idx) * KC + part * NB_MAX + lane;
+#pragma unroll
+        for (int p = 0; p < S; p++)
+          if (p < Se) o[(int64_t)p * Mpad * KC] = __float2bfloat16_rn(dg[p]);
+      }
+    } else {
+      float dre[S], dim[S];
+      double x[L];
+#pragma unroll
+      for (int l = 0; l < L; l++) x[l] = ok ? X.p[(int64_t)l * X.ps + off(t)] : 0.0;
+      digits_of<L>(x, E, dre);
+#pragma unroll
+      for (int l = 0; l < L; l++) x[l] = ok ? X.p[(int64_t)(L + l) * X.ps + off(t)] : 0.0;
+      digits_of<L>(x, E, dim);
+      __nv_bfloat16 *o0 = bs + (((int64_t)c * S) * Npad + 2 * idx) * KC;
+      __nv_bfloat16 *o1 = o0 + KC;
+#pragma unroll
+      for (int q = 0; q < S; q++) {
+        if (q >= Se) break;
+        const int64_t so = (int64_t)q * Npad * KC;
+        o0[so + lane] = __float2bfloat16_rn(dre[q]);
+        o0[so + NB_MAX + lane] = __float2bfloat16_rn(-dim[q]);
+        o1[so + lane] = __float2bfloat16_rn(dim[q]);
+        o1[so + NB_MAX + lane] = __float2bfloat16_rn(dre[q]);
+      }
+    }
   }
 }
 
@@ -668,7 +664,7 @@ __device__ __forceinline__ bool fold_diagonals(uint32_t (&F)[NH][Cfg<L>::FW], ui
 // ---------------------------------------------------------------- GEMM --
 
 // C (m x n complex) = C - A B (BETA) or A B, from the slices of A (rows) and
-// B (columns) cut by k_oz_split_a / k_oz_split_b.  Persistent: one CTA per SM
+// B (columns) cut by k_oz_split_ab.  Persistent: one CTA per SM
 // walks the (row tile, column tile) grid.  Warp 0 lane 0: TMA producer of
 // the A slices (NST-stage ring).  Warp 1: TMEM owner and MMA issuer (lane 0).
 // Warp 2 lane 0: TMA producer of the B slices (NSB chunk buffers, so the next
@@ -969,15 +965,9 @@ int split(View A, View B, int64_t m, int64_t n, int64_t k, void *ws, cudaStream_
   __nv_bfloat16 *bs = (__nv_bfloat16 *)(w + z.a_bytes);
   int *Ea = (int *)(w + z.a_bytes + z.b_bytes);
   int *Eb = Ea + z.Mpad;
-  k_oz_scales<L><<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A, m, k, true, Ea);
-  note();
-  k_oz_scales<L><<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(B, n, k, false, Eb);
-  note();
-  k_oz_split_a<L><<<dim3((unsigned)((z.Mpad * 32 + 255) / 256), (unsigned)z.nchunks), 256, 0, s>>>(A, m, k, Ea, as,
-                                                                                                    z.Mpad, Se);
-  note();
-  k_oz_split_b<L><<<dim3((unsigned)((z.Npad / 2 * 32 + 255) / 256), (unsigned)z.nchunks), 256, 0, s>>>(
-      B, k, n, Eb, bs, z.Npad, Se);
+  const int64_t warps = z.Mpad + z.Npad / 2;
+  k_oz_split_ab<L><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(A, B, m, n, k, Ea, Eb, as, bs, z.Mpad, z.Npad,
+                                                                        (int)z.nchunks, Se);
   note();
   return (int)cudaGetLastError();
 }
