@@ -651,12 +651,11 @@ int tri_solve(View A, int64_t n, const double *W, View R, View Y, int64_t nrhs, 
 }
 
 // The same substitution as one persistent cooperative launch per right-hand
-// side (k_trsv_flow).  flags: nblk ints, all below flagbase + 1 on entry.
-// Returns 1 when the grid cannot be co-resident (the caller falls back to
-// tri_solve).
+// side (k_trsv_flow).  Y: packed planes (Y.ps = Y.ld nrhs); it is filled
+// with FLOW_SENT first.  status: OR-ed with 1 if a wait ran out.  Returns 1
+// when the grid cannot be co-resident (the caller falls back to tri_solve).
 template <int L, bool LOWER, bool CONJT>
-int tri_solve_flow(View A, int64_t n, const double *W, View R, View Y, int64_t nrhs, int *flags, int flagbase,
-                   int *status, cudaStream_t s) {
+int tri_solve_flow(View A, int64_t n, const double *W, View R, View Y, int64_t nrhs, int *status, cudaStream_t s) {
   const int sms = oz::sm_count();
   const int64_t nblk = cdiv(n, SOLVE_BS);
   const int G = (int)std::min<int64_t>(sms, nblk);
@@ -670,13 +669,18 @@ int tri_solve_flow(View A, int64_t n, const double *W, View R, View Y, int64_t n
   int occ = 0;
   MCLU_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trsv_flow<L, LOWER, CONJT>, FLOW_T, smem));
   if ((int64_t)occ * sms < G) return 1;
+  {  // every word of the solution starts as FLOW_SENT
+    const int64_t words = 2 * L * Y.ps;
+    k_fill_u64<<<(unsigned)cdiv(words, 256), 256, 0, s>>>(reinterpret_cast<unsigned long long *>(Y.p), words,
+                                                           FLOW_SENT);
+    MCLU_LAUNCHED();
+  }
   for (int64_t c = 0; c < nrhs; c++) {
     View Rc{R.p + c * R.ld, R.ld, R.ps}, Yc{Y.p + c * Y.ld, Y.ld, Y.ps};
     int64_t a_n = n;
     const double *a_W = W;
-    int *a_flags = flags, *a_status = status;
-    int a_val = flagbase + 1 + (int)c;
-    void *args[] = {&A, &a_n, &a_W, &Rc, &Yc, &a_flags, &a_val, &a_status};
+    int *a_status = status;
+    void *args[] = {&A, &a_n, &a_W, &Rc, &Yc, &a_status};
     MCLU_TRY(cudaLaunchCooperativeKernel((const void *)k_trsv_flow<L, LOWER, CONJT>, dim3(G), dim3(FLOW_T), args, smem,
                                          s));
     note_launch();
@@ -713,7 +717,7 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
   Workspace w;
   MCLU_TRY(w.alloc(perm_bytes + rdiag_bytes + 2 * inv_bytes + 2 * vec_bytes + flag_bytes, s));
   char *cur = (char *)w.p;
-  int *flags = (int *)cur;  // nblk step flags, then the status word
+  int *flags = (int *)cur;  // the status word of the dataflow substitutions at flags[nblk]
   cur += flag_bytes;
   MCLU_TRY(cudaMemsetAsync(flags, 0, (size_t)(nblk + 1) * sizeof(int), s));
   int32_t *perm = (int32_t *)cur;
@@ -741,10 +745,10 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
   if (!conj) {
     k_permute<L><<<pg, 256, 0, s>>>(B, X, perm, n, nrhs, 0);  // X = P B
     MCLU_LAUNCHED();
-    int rc = tri_solve_flow<L, true, false>(A, n, WL, X, Y, nrhs, flags, 0, flags + nblk, s);  // L y = P b
+    int rc = tri_solve_flow<L, true, false>(A, n, WL, X, Y, nrhs, flags + nblk, s);  // L y = P b
     if (rc == 1) rc = tri_solve<L, true, false>(A, n, WL, X, Y, nrhs, s);
     if (rc) return rc;
-    rc = tri_solve_flow<L, false, false>(A, n, WU, Y, X, nrhs, flags, (int)nrhs, flags + nblk, s);  // U x = y
+    rc = tri_solve_flow<L, false, false>(A, n, WU, Y, X, nrhs, flags + nblk, s);  // U x = y
     if (rc == 1) rc = tri_solve<L, false, false>(A, n, WU, Y, X, nrhs, s);
     if (rc) return rc;
     MCLU_TRY(cudaMemcpy2DAsync(Bp, ldb * sizeof(double), X.p, n * sizeof(double), n * sizeof(double),
@@ -752,10 +756,10 @@ int getrs(char trans, int64_t n, int64_t nrhs, const double *Ap, int64_t lda, co
   } else {
     MCLU_TRY(cudaMemcpy2DAsync(X.p, n * sizeof(double), Bp, ldb * sizeof(double), n * sizeof(double),
                                (size_t)2 * L * nrhs, cudaMemcpyDeviceToDevice, s));
-    int rc = tri_solve_flow<L, true, true>(A, n, WU, X, Y, nrhs, flags, 0, flags + nblk, s);  // U^H w = b
+    int rc = tri_solve_flow<L, true, true>(A, n, WU, X, Y, nrhs, flags + nblk, s);  // U^H w = b
     if (rc == 1) rc = tri_solve<L, true, true>(A, n, WU, X, Y, nrhs, s);
     if (rc) return rc;
-    rc = tri_solve_flow<L, false, true>(A, n, WL, Y, X, nrhs, flags, (int)nrhs, flags + nblk, s);  // L^H z = w
+    rc = tri_solve_flow<L, false, true>(A, n, WL, Y, X, nrhs, flags + nblk, s);  // L^H z = w
     if (rc == 1) rc = tri_solve<L, false, true>(A, n, WL, Y, X, nrhs, s);
     if (rc) return rc;
     k_permute<L><<<pg, 256, 0, s>>>(X, B, perm, n, nrhs, 1);  // B = P^T z

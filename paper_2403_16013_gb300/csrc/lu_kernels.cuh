@@ -980,17 +980,19 @@ __global__ void __launch_bounds__(256) k_blk_solve(View A, int64_t k0, int bs, c
 // The whole forward (LOWER) or backward substitution of one right-hand side
 // in one cooperative launch.  Step q (q = 0 .. nblk-1) makes x of diagonal
 // block b(q) = q (LOWER) or nblk-1-q.  CTA g owns the steps q = g (mod G):
-// the residual of its blocks lives in its shared memory for the whole solve.
-// Iteration q of every CTA:
-//   1. get x_q: the owner has it; the others wait for flags[q] (acquire,
-//      bounded spin) and read it from Y;
-//   2. the owner of step q+1 (warp 0) subtracts op(T)(b(q+1), b(q)) x_q from
-//      its block, forms x_{q+1} = op(W_{b(q+1)}) r_{b(q+1)}, stores it in Y and
-//      releases flags[q+1] -- before any other work, since every CTA waits
-//      for it;
-//   3. all other owned blocks of later steps subtract op(T)(block, b(q)) x_q.
-// The owner of q+1 reads the T tile and W block for step 2 before it waits.
-// A wait that runs out (the co-resident cooperative launch rules this out)
+// the residual of its blocks lives in its shared memory for the whole solve,
+// and so does M_q = op(W_{b(q)}) op(T)(b(q), b(q-1)) of each owned step,
+// formed at the start.  Iteration q of every CTA:
+//   1. the owner of step q+1 forms y = op(W_{b(q+1)}) r_{b(q+1)} (all its
+//      earlier terms are in) before it needs x_q;
+//   2. get x_q: the owner has it; the others poll its words in Y until none
+//      holds FLOW_SENT any more (every word validates itself: no flag, no
+//      fence, one round trip);
+//   3. the owner of step q+1 forms x_{q+1} = y - M_{q+1} x_q and stores it --
+//      before any other work, since every CTA waits for it;
+//   4. all other owned blocks of later steps subtract op(T)(block, b(q)) x_q.
+// Y must hold FLOW_SENT in every word of the solution before the launch.  A
+// wait that runs out (the co-resident cooperative launch rules this out)
 // sets *status and writes NaN to every x the CTA still owed, so the failure
 // shows in the result.
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -1001,9 +1003,29 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 __device__ __forceinline__ void st_release(int *p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Every 64-bit word of count words at p set to v.
+static __global__ void k_fill_u64(unsigned long long *p, int64_t count, unsigned long long v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) p[i] = v;
+}
 
 constexpr int FLOW_T = 128;
-constexpr long long FLOW_WAIT = 2000000000LL;  // bound on one flag wait, ~1 s at 2 GHz
+constexpr long long FLOW_WAIT = 2000000000LL;  // bound on one wait, ~1 s at 2 GHz
+// The value of a solution word not yet written: a signalling-NaN bit pattern,
+// which no arithmetic result has (a NaN result is a quiet NaN).
+constexpr unsigned long long FLOW_SENT = 0x7ff0dead5eed0000ULL;
 
 // One warp: lane = 4 i + g handles row i (< SOLVE_BS) and the products j = g, g+4.
 template <int L, bool CONJT>
@@ -1178,15 +1200,16 @@ __device__ __forceinline__ void combine_parts(const double *part, const double (
   }
 }
 
-// Shared memory of k_trsv_flow for nown owned blocks.
+// Shared memory of k_trsv_flow for nown owned blocks: residuals, x of two
+// steps, the M blocks.
 template <int L>
 constexpr size_t trsv_flow_smem(int nown) {
-  return ((size_t)nown + 2) * SOLVE_BS * 2 * L * sizeof(double);
+  return (((size_t)nown + 2) * SOLVE_BS + (size_t)nown * SOLVE_BS * SOLVE_BS) * 2 * L * sizeof(double);
 }
 
 template <int L, bool LOWER, bool CONJT>
 __global__ void __launch_bounds__(FLOW_T) k_trsv_flow(View A, int64_t n, const double *Winv, View R, View Y,
-                                                      int *flags, int flagval, int *status) {
+                                                      int *status) {
   constexpr int BS = SOLVE_BS;
   extern __shared__ double fsm[];
   const int G = (int)gridDim.x, g = (int)blockIdx.x;
@@ -1195,15 +1218,20 @@ __global__ void __launch_bounds__(FLOW_T) k_trsv_flow(View A, int64_t n, const d
   const int nown = (nblk - g + G - 1) / G;  // owned steps q = g + i G, i < nown
   double(*res)[BS][2 * L] = reinterpret_cast<double(*)[BS][2 * L]>(fsm);
   double(*xs)[BS][2 * L] = res + nown;  // [2][BS][2L], by step parity
+  double(*Ms)[BS][BS][2 * L] = reinterpret_cast<double(*)[BS][BS][2 * L]>(xs + 2);  // [nown]
   __shared__ int s_ok;
+  __shared__ double s_part[4 * SOLVE_BS * L];
   auto blk = [&](int q) -> int64_t { return LOWER ? q : nblk - 1 - q; };
   auto rows = [&](int q) -> int { return (int)min((int64_t)BS, n - blk(q) * BS); };
   auto wblk = [&](int q) -> const double * { return Winv + blk(q) * 2 * L * BS * BS; };
-  auto publish = [&](int q, const double (*x)[2 * L]) {  // warp 0: store x_q, release flags[q]
-    if (lane < rows(q)) stz<L>(Y, blk(q) * BS + lane, 0, lds_z<L>(x[lane]));
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) st_release(flags + q, flagval);
+  auto yword = [&](int q, int t) -> unsigned long long * {  // word t = plane * rows + row of x_q in Y
+    const int rq = rows(q);
+    return reinterpret_cast<unsigned long long *>(Y.p + (int64_t)(t / rq) * Y.ps + blk(q) * BS + t % rq);
+  };
+  auto publish = [&](int q, const double (*x)[2 * L]) {  // warp 0: the words of x_q to Y
+    const int rq = rows(q);
+    for (int t = lane; t < rq * 2 * L; t += 32)
+      st_relaxed_u64(yword(q, t), (unsigned long long)__double_as_longlong(x[t % rq][t / rq]));
   };
   auto fail_rest = [&](int qfrom) {  // NaN into every x this CTA still owed
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
@@ -1219,6 +1247,45 @@ __global__ void __launch_bounds__(FLOW_T) k_trsv_flow(View A, int64_t n, const d
     const int64_t row = blk(q) * BS + r;
     sts_z<L>(res[i][r], r < rows(q) ? ldz<L>(R, row, 0) : z_zero<L>());
   }
+  // M_q = op(W_q) op(T)(b(q), b(q-1)) of every owned step q >= 1: thread t
+  // forms part t & 1 (re, im) of entry (e >> 3, e & 7), e = t >> 1
+  for (int i = 0; i < nown; i++) {
+    const int q = g + i * G;
+    if (q == 0) continue;
+    const int br = rows(q), bc = rows(q - 1);
+    const int e = tid >> 1, part = tid & 1, ei = e >> 3, ej = e & 7;
+    const double *Wb = wblk(q);
+    const int64_t r0 = blk(q) * BS, c0 = blk(q - 1) * BS;
+    Acc<L> acc;
+    acc.zero();
+    if (ei < br && ej < bc) {
+      for (int k = 0; k < br; k++) {
+        if (LOWER ? k > ei : k < ei) continue;  // op(W) is triangular
+        Z<L> w;
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+          if (CONJT) {
+            w.re.x[l] = Wb[((size_t)l * BS + k) * BS + ei];
+            w.im.x[l] = flip(Wb[((size_t)(L + l) * BS + k) * BS + ei]);
+          } else {
+            w.re.x[l] = Wb[((size_t)l * BS + ei) * BS + k];
+            w.im.x[l] = Wb[((size_t)(L + l) * BS + ei) * BS + k];
+          }
+        }
+        const Z<L> t = CONJT ? z_conj<L>(ldz<L>(A, c0 + ej, r0 + k)) : ldz<L>(A, r0 + k, c0 + ej);
+        if (part == 0) {
+          acc.template add_prod<false>(w.re, t.re);
+          acc.template add_prod<true>(w.im, t.im);
+        } else {
+          acc.template add_prod<false>(w.re, t.im);
+          acc.template add_prod<false>(w.im, t.re);
+        }
+      }
+    }
+    const auto v = acc.result();
+#pragma unroll
+    for (int l = 0; l < L; l++) Ms[i][ei][ej][part * L + l] = v.x[l];
+  }
   __syncthreads();
   if (g == 0 && warp == 0) {  // step 0 needs no update
     InvRegs<L, LOWER, CONJT> w;
@@ -1232,50 +1299,62 @@ __global__ void __launch_bounds__(FLOW_T) k_trsv_flow(View A, int64_t n, const d
     const int par = q & 1;
     const int qn = q + 1;
     const bool crit = qn < nblk && qn % G == g;
-    TileRegs<L, CONJT> tcrit;
-    InvRegs<L, LOWER, CONJT> wcrit;
-    if (crit) {  // operands of step 2, read before the wait (every warp)
-      tcrit.load(A, blk(qn) * BS, blk(q) * BS, rows(qn), rows(q), lane);
-      wcrit.load(wblk(qn), rows(qn), lane);
+    const int ic = crit ? (qn - g) / G : 0;
+    // 1. y = op(W) r of the next step's block, in place
+    if (crit) {
+      InvRegs<L, LOWER, CONJT> w;
+      w.load(wblk(qn), rows(qn), lane);
+      warp_part<L, true>(w.w, res[ic], s_part, warp, rows(qn), rows(qn), LOWER, true, lane);
+      __syncthreads();
+      combine_parts<L>(s_part, nullptr, res[ic], rows(qn), warp, lane);
+      __syncthreads();
     }
-    if (q % G != g) {  // 1. wait for x_q
-      if (tid == 0) {
-        int ok = 1;
+    // 2. x_q
+    if (q % G != g) {
+      if (warp == 0) {
+        const int nw = rows(q) * 2 * L;  // <= 64 words
+        unsigned long long v0 = FLOW_SENT, v1 = FLOW_SENT;
+        bool ok = true;
         const long long t0 = clock64();
-        while (ld_acquire(flags + q) != flagval) {
-          if (clock64() - t0 > FLOW_WAIT) {
-            ok = 0;
-            atomicOr(status, 1);
+        for (;;) {
+          if (lane < nw && v0 == FLOW_SENT) v0 = ld_relaxed_u64(yword(q, lane));
+          if (lane + 32 < nw && v1 == FLOW_SENT) v1 = ld_relaxed_u64(yword(q, lane + 32));
+          const bool need = (lane < nw && v0 == FLOW_SENT) || (lane + 32 < nw && v1 == FLOW_SENT);
+          if (!__any_sync(0xffffffffu, need)) break;
+          if (__any_sync(0xffffffffu, clock64() - t0 > FLOW_WAIT)) {
+            ok = false;
             break;
           }
         }
-        s_ok = ok;
+        const int rq = rows(q);
+        if (lane < nw) xs[par][lane % rq][lane / rq] = __longlong_as_double((long long)v0);
+        if (lane + 32 < nw) xs[par][(lane + 32) % rq][(lane + 32) / rq] = __longlong_as_double((long long)v1);
+        if (lane == 0) {
+          s_ok = ok ? 1 : 0;
+          if (!ok) atomicOr(status, 1);
+        }
       }
       __syncthreads();
       if (!s_ok) {
         fail_rest(q);
         return;
       }
-      const int rq = rows(q);
-      for (int t = tid; t < rq * 2 * L; t += FLOW_T)
-        xs[par][t % rq][t / rq] = __ldcg(Y.p + (int64_t)(t / rq) * Y.ps + blk(q) * BS + t % rq);
-      __syncthreads();
     }
-    // 2. the next step's block first, its products split over the four warps
+    // 3. x_{q+1} = y - M x_q, its products split over the four warps
     if (crit) {
-      __shared__ double s_part[4 * SOLVE_BS * L];
-      const int i = (qn - g) / G;
-      warp_part<L, false>(tcrit.t, xs[par], s_part, warp, rows(qn), rows(q), false, false, lane);
+      Z<L> mt[2];
+      {
+        const int i = lane >> 2, gq = lane & 3;
+#pragma unroll
+        for (int h = 0; h < 2; h++) mt[h] = lds_z<L>(Ms[ic][i][gq + 4 * h]);
+      }
+      warp_part<L, false>(mt, xs[par], s_part, warp, rows(qn), rows(q), false, false, lane);
       __syncthreads();
-      combine_parts<L>(s_part, res[i], res[i], rows(qn), warp, lane);
-      __syncthreads();
-      warp_part<L, true>(wcrit.w, res[i], s_part, warp, rows(qn), rows(qn), LOWER, true, lane);
-      __syncthreads();
-      combine_parts<L>(s_part, nullptr, xs[par ^ 1], rows(qn), warp, lane);
+      combine_parts<L>(s_part, res[ic], xs[par ^ 1], rows(qn), warp, lane);
       __syncthreads();
       if (warp == 0) publish(qn, xs[par ^ 1]);
     }
-    // 3. the other owned blocks of later steps
+    // 4. the other owned blocks of later steps
     {
       int k = 0;
       for (int i = 0; i < nown; i++) {

@@ -124,17 +124,6 @@ constexpr unsigned long long KEY_STAMP_MASK = (1ull << KEY_STAMP_BITS) - 1;
 // exact keys; 2^23 units of the order key is 2^-30 or more.
 constexpr long long KEY_SLOT_NEAR = 1ll << 23;
 
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
 
 template <int L>
 __device__ __forceinline__ int *slot_stamp2(double *slot) {
