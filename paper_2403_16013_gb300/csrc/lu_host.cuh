@@ -126,6 +126,7 @@ constexpr size_t getrf_ws_bytes(int64_t n, int nb, bool m3) {
   b += ((2 * 2 * L * nbc * sizeof(double)) + 255) & ~(size_t)255;                    // srow
   b += ((2 * COOP_GMAX * sizeof(int)) + 255) & ~(size_t)255;                          // rcp_flag
   b += ((2 * COOP_GMAX * COOP_KS * sizeof(double)) + 255) & ~(size_t)255;              // kslot
+  b += ((2 * COOP_GMAX * 2 * L * sizeof(double)) + 255) & ~(size_t)255;                // vnext
   if (m3) b += 2 * ((((size_t)n * nb * L * sizeof(double)) + 255) & ~(size_t)255);  // 3M pre-sums
   return b + 1024;
 }
@@ -192,8 +193,9 @@ int launch_panel_coop(View A, int64_t n, int64_t j0, int64_t jend, int32_t *ipiv
   int G = (int)std::min<int64_t>({(int64_t)sms, cdiv(m, 8), (int64_t)COOP_GMAX});
   if (G < 1) G = 1;
   const int rpc = (int)cdiv(m, G);
-  // owned rows + the pivot rows of two columns + the multipliers' partial products
-  const size_t smem = (((size_t)rpc + 2) * nb * 2 * L + (size_t)4 * rpc * L) * sizeof(double);
+  // owned rows + the pivot rows of two columns + the partial products of the
+  // multipliers and of the next column (DD), of the multipliers (TD, QD)
+  const size_t smem = (((size_t)rpc + 2) * nb * 2 * L + (size_t)(L == 2 ? 8 : 4) * rpc * L) * sizeof(double);
   if (smem > 200 * 1024) return 1;
   auto kern = L == 2 ? k_panel_coop<L> : k_panel_team<L>;
   static std::atomic<unsigned long long> attr{0};
@@ -430,6 +432,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   cw.prow = cv.take<double>((size_t)2 * COOP_GMAX * 2 * L * nbc);
   cw.srow = cv.take<double>((size_t)2 * 2 * L * nbc);
   cw.rcp_flag = cv.take<int>((size_t)2 * COOP_GMAX);
+  cw.vnext = cv.take<double>((size_t)2 * COOP_GMAX * 2 * L);
   double *sumL = nullptr, *sumU = nullptr;
   if (m3) {
     sumL = cv.take<double>((size_t)n * nb * L);

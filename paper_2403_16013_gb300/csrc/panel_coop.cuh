@@ -26,6 +26,8 @@
 //   4. every CTA scales its rows below j by the winner's reciprocal (the
 //      multipliers) and updates column j+1 of those rows, renormalised for
 //      the next keys; the other columns wait for step 2 of the next column.
+//      (DD: the candidate also publishes v = r u_{j,j+1}, so that column j+1
+//      is a_{i,j+1} - a_ij v, formed at the same time as the multipliers.)
 // Updated elements stay in leveled-accumulator form (no renormalisation)
 // except the next pivot column; rows are renormalised when written back.
 // Slots, row buffers and pivot rows alternate between two buffers by column
@@ -50,6 +52,7 @@ struct CoopWS {
   double *prow;   // [2][G][nb][2L] best row of each CTA, by column parity
   double *srow;   // [2][nb][2L] row j, by column parity
   int *rcp_flag;  // [2G] column stamp (j + 1) of the reciprocal and rows of each slot
+  double *vnext;  // [2G][2L] v = r u of each slot's candidate, u its element in the next column (DD)
 };
 
 // Barrier over the `count` threads (whole warps) that execute it with this id
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     stp(r, c, ldz<L>(A, rbeg + r, j0 + c));
   }
   __shared__ int s_zero, s_next, s_pend, s_ok, s_cand, s_fast;
-  __shared__ double s_rcp[2 * L], s_key[L], s_k0;
+  __shared__ double s_rcp[2 * L], s_v[2 * L], s_key[L], s_k0;
   // The CTA's candidate for panel column c among its rows i >= jrow: the
   // largest k0 (one FP64 addition per row), unless another row's k0 is near
   // it; then the full keys of the near rows decide (s_fast = 0, s_key the
@@ -461,6 +464,8 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     //    (it needs no FP64 unit until the swap).  The rest of the pending
     //    update goes in 32-element pieces to whole warps: 6 at once, the
     //    others when free.
+    __shared__ double s_r[2 * L];  // this CTA's candidate's reciprocal (re limbs, im limbs)
+    const bool vnx = L == 2 && has && jc + 1 < nb;  // publish v = r u_{cand, jc+1}
     if ((w & 2) == 0) {
       __shared__ double s_e[2];  // Re e, Im e of the Newton step
       const bool act = has && lane == 0 && w < 2;
@@ -481,7 +486,10 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
           v = w == 0 ? z.re : z.im;
         }
 #pragma unroll
-        for (int l = 0; l < L; l++) ws.part_rcp[(int64_t)q * 2 * L + w * L + l] = v.x[l];
+        for (int l = 0; l < L; l++) {
+          ws.part_rcp[(int64_t)q * 2 * L + w * L + l] = v.x[l];
+          s_r[w * L + l] = v.x[l];
+        }
       }
       named_sync(1, 128);
       if (w == 5 && lane == 0 && has && fast)  // off the reciprocal's SMSPs' critical window
@@ -520,6 +528,29 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     }
     if (w == 0 || w == 1 || w == 2 || w == 7) {
       named_sync(2, 128);
+      if (vnx && w < 2) {
+        // v = r u on warps 0 (Re) and 1 (Im), u the candidate row's element
+        // of column jc+1 (final: warp 2 updated it)
+        if (lane == 0) {
+          const Z<L> u = ldp(cr, jc + 1);
+          R<L> rre, rim;
+#pragma unroll
+          for (int l = 0; l < L; l++) {
+            rre.x[l] = s_r[l];
+            rim.x[l] = s_r[L + l];
+          }
+          Acc<L> t;
+          t.set_prod(rre, w == 0 ? u.re : u.im);
+          if (w == 0)
+            t.template add_prod<true>(rim, u.im);
+          else
+            t.template add_prod<false>(rim, u.re);
+          const R<L> v = t.result();
+#pragma unroll
+          for (int l = 0; l < L; l++) cw.vnext[(int64_t)q * 2 * L + w * L + l] = v.x[l];
+        }
+        named_sync(6, 64);
+      }
       if (has && tid == 0) {
         st_release(cw.rcp_flag + q, (int)(j + 1));
       }
@@ -547,6 +578,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         const double *prow = cw.prow + (size_t)part * RW;
         for (int t = lane; t < RW; t += 32) su[t] = __ldcg(prow + t);
         if (lane < 2 * L) s_rcp[lane] = __ldcg(ws.part_rcp + (int64_t)part * 2 * L + lane);
+        if (L == 2 && jc + 1 < nb && lane < 2 * L) s_v[lane] = __ldcg(cw.vnext + (int64_t)part * 2 * L + lane);
       }
       named_sync(3, 96);  // warps 2 and 7 are done with rows cr and jr
       if (ok && !zero) {
@@ -624,24 +656,9 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         r.re.x[l] = s_rcp[l];
         r.im.x[l] = s_rcp[L + l];
       }
-      // 4. multipliers l = a r of the rows below j: warps 0..3 (one per
-      //    SMSP, each with its own FP64 unit) form the four real products
-      //    Re a Re r, Im a Im r, Re a Im r, Im a Re r on leveled
-      //    accumulators; warps 0 and 1 then form Re l = P0 - P1 and
-      //    Im l = P2 + P3
-      if (w < 4) {
-        const R<L> y = (w == 0 || w == 3) ? r.re : r.im;
-        for (int rr = lane; rr < nr; rr += 32) {
-          if (rbeg + rr <= j) continue;
-          const Z<L> a = ldp(rr, jc);
-          Acc<L> t;
-          t.set_prod((w == 0 || w == 2) ? a.re : a.im, y);
-#pragma unroll
-          for (int l = 0; l < L; l++) mscr[((size_t)w * rpc + rr) * L + l] = t.s[l];
-        }
-      }
-      __syncthreads();
-      if (w < 2) {
+      // the multipliers' combination (warps 0 and 1): Re l = P0 - P1,
+      // Im l = P2 + P3, written to column jc
+      auto combine_l = [&]() {
         for (int rr = lane; rr < nr; rr += 32) {
           if (rbeg + rr <= j) continue;
           Acc<L> t, o;
@@ -656,46 +673,78 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
 #pragma unroll
           for (int l = 0; l < L; l++) d[(size_t)l * rpc] = v.x[l];
         }
-      }
-      __syncthreads();
-      // the next pivot column jc+1 now, renormalised for its keys (the
-      // columns after it wait for the next column's step 2), split like the
-      // multipliers: warps 0..3 form Re l Re u, Im l Im u, Re l Im u,
-      // Im l Re u; warps 0 and 1 take a - P0 + P1 and a - P2 - P3
-      if (jc + 1 < nb) {
-        const int cc = jc + 1;
-        if (w < 4) {
-          R<L> y;
+      };
+      // column cc's part h (0: Re, 1: Im) from the products P_{b+2h},
+      // P_{b+2h+1}: Re a - P0 + P1, Im a - P2 - P3, renormalised for its keys
+      auto combine_next = [&](int cc, int h, int b) {
+        for (int rr = lane; rr < nr; rr += 32) {
+          if (rbeg + rr <= j) continue;
+          const Z<L> a = ldp(rr, cc);
+          Acc<L> t, o;
+          t.set(h == 0 ? a.re : a.im);
 #pragma unroll
-          for (int l = 0; l < L; l++) y.x[l] = su[cc * 2 * L + ((w == 0 || w == 3) ? 0 : L) + l];
-          for (int rr = lane; rr < nr; rr += 32) {
-            if (rbeg + rr <= j) continue;
-            const Z<L> lv = ldp(rr, jc);
-            Acc<L> t;
-            t.set_prod((w == 0 || w == 2) ? lv.re : lv.im, y);
+          for (int l = 0; l < L; l++) o.s[l] = mscr[((size_t)(b + 2 * h) * rpc + rr) * L + l];
+          t.add_acc(o, true);
 #pragma unroll
-            for (int l = 0; l < L; l++) mscr[((size_t)w * rpc + rr) * L + l] = t.s[l];
-          }
+          for (int l = 0; l < L; l++) o.s[l] = mscr[((size_t)(b + 2 * h + 1) * rpc + rr) * L + l];
+          t.add_acc(o, h == 1);
+          const R<L> v = t.result();
+          double *d = sp + (size_t)cc * 2 * L * rpc + rr + (size_t)(h * L) * rpc;
+#pragma unroll
+          for (int l = 0; l < L; l++) d[(size_t)l * rpc] = v.x[l];
         }
+      };
+      // product p of x (0: Re x Re y, 1: Im x Im y, 2: Re x Im y, 3: Im x Re y)
+      // for the rows below j into mscr[slot]
+      auto products = [&](int p, int slot, int c, const double *y2) {
+        R<L> y;
+#pragma unroll
+        for (int l = 0; l < L; l++) y.x[l] = y2[((p == 0 || p == 3) ? 0 : L) + l];
+        for (int rr = lane; rr < nr; rr += 32) {
+          if (rbeg + rr <= j) continue;
+          const Z<L> x = ldp(rr, c);
+          Acc<L> t;
+          t.set_prod((p == 0 || p == 2) ? x.re : x.im, y);
+#pragma unroll
+          for (int l = 0; l < L; l++) mscr[((size_t)slot * rpc + rr) * L + l] = t.s[l];
+        }
+      };
+      if (L == 2 && jc + 1 < nb) {
+        // 4. (DD) the multipliers l = a r and column jc+1 = a' - a v at once:
+        //    warps 0..3 (one per SMSP) form the four real products of a r,
+        //    warps 4..7 those of a v; then warps 0 and 1 combine l while
+        //    warps 2 and 3 combine column jc+1
+        const int cc = jc + 1;
+        products(w & 3, w, jc, w < 4 ? s_rcp : s_v);
         __syncthreads();
-        if (w < 2) {
-          for (int rr = lane; rr < nr; rr += 32) {
-            if (rbeg + rr <= j) continue;
-            const Z<L> a = ldp(rr, cc);
-            Acc<L> t, o;
-            t.set(w == 0 ? a.re : a.im);
-#pragma unroll
-            for (int l = 0; l < L; l++) o.s[l] = mscr[((size_t)(2 * w) * rpc + rr) * L + l];
-            t.add_acc(o, true);
-#pragma unroll
-            for (int l = 0; l < L; l++) o.s[l] = mscr[((size_t)(2 * w + 1) * rpc + rr) * L + l];
-            t.add_acc(o, w == 1);
-            const R<L> v = t.result();
-            double *d = sp + (size_t)cc * 2 * L * rpc + rr + (size_t)(w * L) * rpc;
-#pragma unroll
-            for (int l = 0; l < L; l++) d[(size_t)l * rpc] = v.x[l];
-          }
-          if (fused) {  // column cc is final on warps 0 and 1: the next candidate
+        if (w < 2)
+          combine_l();
+        else if (w < 4)
+          combine_next(cc, w - 2, 4);
+        if (fused && w < 4) {  // column cc is final on warps 0..3: the next candidate
+          named_sync(5, 128);
+          if (w == 0) select_warp0(cc, j + 1);
+        }
+      } else {
+        // 4. multipliers l = a r of the rows below j: warps 0..3 (one per
+        //    SMSP, each with its own FP64 unit) form the four real products
+        //    Re a Re r, Im a Im r, Re a Im r, Im a Re r on leveled
+        //    accumulators; warps 0 and 1 then form Re l = P0 - P1 and
+        //    Im l = P2 + P3
+        if (w < 4) products(w, w, jc, s_rcp);
+        __syncthreads();
+        if (w < 2) combine_l();
+        __syncthreads();
+        // the next pivot column jc+1 now, renormalised for its keys (the
+        // columns after it wait for the next column's step 2), split like
+        // the multipliers: warps 0..3 form Re l Re u, Im l Im u, Re l Im u,
+        // Im l Re u; warps 0 and 1 take a - P0 + P1 and a - P2 - P3
+        if (jc + 1 < nb) {
+          const int cc = jc + 1;
+          if (w < 4) products(w, w, jc, su + cc * 2 * L);
+          __syncthreads();
+          if (w < 2) combine_next(cc, w, 0);
+          if (fused && w < 2) {  // column cc is final on warps 0 and 1: the next candidate
             named_sync(5, 64);
             if (w == 0) select_warp0(cc, j + 1);
           }
