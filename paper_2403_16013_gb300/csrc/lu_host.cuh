@@ -127,6 +127,7 @@ constexpr size_t getrf_ws_bytes(int64_t n, int nb, bool m3) {
   b += ((2 * COOP_GMAX * sizeof(int)) + 255) & ~(size_t)255;                          // rcp_flag
   b += ((2 * COOP_GMAX * COOP_KS * sizeof(double)) + 255) & ~(size_t)255;              // kslot
   b += ((2 * COOP_GMAX * 2 * L * sizeof(double)) + 255) & ~(size_t)255;                // vnext
+  b += ((2 * COOP_GMAX * sizeof(int)) + 255) & ~(size_t)255;                           // v_flag
   if (m3) b += 2 * ((((size_t)n * nb * L * sizeof(double)) + 255) & ~(size_t)255);  // 3M pre-sums
   return b + 1024;
 }
@@ -433,6 +434,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   cw.srow = cv.take<double>((size_t)2 * 2 * L * nbc);
   cw.rcp_flag = cv.take<int>((size_t)2 * COOP_GMAX);
   cw.vnext = cv.take<double>((size_t)2 * COOP_GMAX * 2 * L);
+  cw.v_flag = cv.take<int>((size_t)2 * COOP_GMAX);
   double *sumL = nullptr, *sumU = nullptr;
   if (m3) {
     sumL = cv.take<double>((size_t)n * nb * L);
@@ -445,6 +447,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   int *oz_status = ws.zflag + 1;  // spare word of the header block
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
   MCLU_TRY(cudaMemsetAsync(cw.rcp_flag, 0, (size_t)2 * COOP_GMAX * sizeof(int), s));
+  MCLU_TRY(cudaMemsetAsync(cw.v_flag, 0, (size_t)2 * COOP_GMAX * sizeof(int), s));
   MCLU_TRY(cudaMemsetAsync(cw.kslot, 0, (size_t)2 * COOP_GMAX * COOP_KS * sizeof(double), s));
   View A{Ap, lda, lda * n};
 

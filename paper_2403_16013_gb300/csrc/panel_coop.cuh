@@ -53,6 +53,7 @@ struct CoopWS {
   double *srow;   // [2][nb][2L] row j, by column parity
   int *rcp_flag;  // [2G] column stamp (j + 1) of the reciprocal and rows of each slot
   double *vnext;  // [2G][2L] v = r u of each slot's candidate, u its element in the next column (DD)
+  int *v_flag;    // [2G] column stamp (j + 1) of vnext of each slot
 };
 
 // Barrier over the `count` threads (whole warps) that execute it with this id
@@ -334,7 +335,34 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
       z.im.x[q] = im.s[q];
     }
     return z;
+  };  // one component of upd (h = 0: Re, 1: Im), stored in place: the pending
+  // update in items of half the FP64 work, so that a warp that joins late
+  // holds the others up by less
+  auto upd1 = [&](int r, int c, int jm, const double *su, int h) {
+    R<L> ur, ui;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      ur.x[q] = su[c * 2 * L + q];
+      ui.x[q] = su[c * 2 * L + L + q];
+    }
+    const Z<L> lv = ldp(r, jm);
+    double *d = sp + (size_t)c * 2 * L * rpc + r + (size_t)(h * L) * rpc;
+    Acc<L> t;
+    R<L> a;
+#pragma unroll
+    for (int q = 0; q < L; q++) a.x[q] = d[(size_t)q * rpc];
+    t.set(a);
+    if (h == 0) {  // Re a - Re l Re u + Im l Im u
+      t.template add_prod<true>(lv.re, ur);
+      t.template add_prod<false>(lv.im, ui);
+    } else {       // Im a - Re l Im u - Im l Re u
+      t.template add_prod<true>(lv.re, ui);
+      t.template add_prod<true>(lv.im, ur);
+    }
+#pragma unroll
+    for (int q = 0; q < L; q++) d[(size_t)q * rpc] = t.s[q];
   };
+
   // load the owned rows
   for (int t = tid; t < nr * nb; t += COOP_T) {
     const int r = t % nr, c = t / nr;
@@ -528,6 +556,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     }
     if (w == 0 || w == 1 || w == 2 || w == 7) {
       named_sync(2, 128);
+      if (has && tid == 0) st_release(cw.rcp_flag + q, (int)(j + 1));
       if (vnx && w < 2) {
         // v = r u on warps 0 (Re) and 1 (Im), u the candidate row's element
         // of column jc+1 (final: warp 2 updated it)
@@ -550,9 +579,7 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
           for (int l = 0; l < L; l++) cw.vnext[(int64_t)q * 2 * L + w * L + l] = v.x[l];
         }
         named_sync(6, 64);
-      }
-      if (has && tid == 0) {
-        st_release(cw.rcp_flag + q, (int)(j + 1));
+        if (tid == 0) st_release(cw.v_flag + q, (int)(j + 1));
       }
     }
     if (w == 3) {
@@ -578,7 +605,6 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         const double *prow = cw.prow + (size_t)part * RW;
         for (int t = lane; t < RW; t += 32) su[t] = __ldcg(prow + t);
         if (lane < 2 * L) s_rcp[lane] = __ldcg(ws.part_rcp + (int64_t)part * 2 * L + lane);
-        if (L == 2 && jc + 1 < nb && lane < 2 * L) s_v[lane] = __ldcg(cw.vnext + (int64_t)part * 2 * L + lane);
       }
       named_sync(3, 96);  // warps 2 and 7 are done with rows cr and jr
       if (ok && !zero) {
@@ -588,6 +614,11 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
         }
         if (p != j && jr >= 0)
           for (int t = lane; t < RW; t += 32) rowel(jr, t) = su[t];
+        if (L == 2 && jc + 1 < nb) {  // the winner's v, published after its reciprocal
+          if (lane == 0) ok = coop_wait_flag(cw.v_flag + part, (int)(j + 1));
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (ok && lane < 2 * L) s_v[lane] = __ldcg(cw.vnext + (int64_t)part * 2 * L + lane);
+        }
       }
       if (lane == 0) {
         if (!ok) {
@@ -608,16 +639,18 @@ __global__ void __launch_bounds__(COOP_T) k_panel_coop(View A, int64_t n, int64_
     if (w != 3 && pend) {
       const int rlo = (int)max((int64_t)0, j - rbeg);  // rows i > j - 1
       const int nrow = nr - rlo, ncol = nb - jc - 1;
-      const int tot = nrow > 0 ? nrow * ncol : 0;
+      const int per = nrow > 0 ? nrow * ncol : 0;     // elements
+      const int half = (per + 31) / 32 * 32;          // items of one component, whole warps
       for (;;) {
         int base = 0;
         if (lane == 0) base = atomicAdd(&s_next, 32);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= tot) break;
-        const int t = base + lane;
-        if (t < tot) {
+        if (base >= 2 * half) break;
+        const int h = base >= half ? 1 : 0;  // uniform over the warp
+        const int t = base - h * half + lane;
+        if (t < per) {
           const int rr = rlo + t % nrow, cc = jc + 1 + t / nrow;
-          if (rr != cr && rr != jr) stp(rr, cc, upd(rr, cc, jc - 1, sprev));
+          if (rr != cr && rr != jr) upd1(rr, cc, jc - 1, sprev, h);
         }
       }
     }
