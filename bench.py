@@ -65,11 +65,11 @@ OZAKI_S = {"dd": 16, "td": 24, "qd": 32}
 # the n = 4096 DD step: n2 = 3968 rows and columns, K = 256 realified).  It is
 # reported, scaled to the average trailing launch by n2^2, only while the
 # kernel source is the one it was taken on (sha1 of csrc/ozaki.cuh).
-OZ_TRAFFIC = {"dd": {"bytes": 606346752 + 468483840, "n2": 3968, "src_sha1": "4b50dafc85d50e75ec2fff17acf26f58e2302925"}}
+OZ_TRAFFIC = {"dd": {"bytes": 604965120 + 468543232, "n2": 3968, "src_sha1": "bdde21fd20155ef65d5b2e26c12829e015eb3623"}}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one cooperative panel
 # launch (the first 32-column sub-panel of n = 2048: m = 2048 rows), valid
 # while the kernel's source is unchanged
-PANEL_TRAFFIC = {"dd": {"bytes": 2237440 + 14592, "m": 2048, "w": 32, "src_sha1": "d6fc05caa117742aeae43b56a1a6d89c5c052c59"}}
+PANEL_TRAFFIC = {"dd": {"bytes": 2244096 + 39168, "m": 2048, "w": 32, "src_sha1": "c28d79383cdc2fa089319ef508a6aa90a1d22481"}}
 # unit roundoff exponents: u = 2^-104 / 2^-157 / 2^-209
 U_EXP = {"dd": 104, "td": 157, "qd": 209}
 
