@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, Vie
                                                  View X2, int64_t ncol1, int64_t xrow2) {
   const int r = threadIdx.x, p = threadIdx.y;
   const int RT = blockDim.x;
-  const int tid = p * RT + r, nthr = 4 * RT;
+  const int tid = p * RT + r;
   int64_t c = blockIdx.x;
   if (c >= ncol1) {
     X = X2;

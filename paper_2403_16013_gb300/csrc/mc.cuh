@@ -520,8 +520,8 @@ __device__ __forceinline__ Z<L> z_inv(const Z<L> &a) {
 //          binary64 and added to r0 with TwoSum: relative error of order
 //          |e|^3 + 2^-105.
 // The real and imaginary parts of e and of r are independent chains (the
-// panel runs them on two SMSPs).  L >= 3 adds one Newton step
-// r <- r + r (1 - p r) in L-limb arithmetic.
+// panel runs them on two SMSPs).  L >= 3 adds one Newton step in L-limb
+// arithmetic (rcp_prod, rcp_resid_l, rcp_newton below).
 struct RcpSeed {
   double rr, ri;  // Re r0, Im r0
 };
@@ -578,6 +578,87 @@ __device__ __forceinline__ R<L> rcp_finish(const RcpSeed &s, double er, double e
   return r;
 }
 
+// L >= 3: one Newton step from the two-limb r (rcp_finish) to L limbs.
+//   e = 1 - p r with the four real products P_xy = p_x r_y (x, y in re, im;
+//   p_x L limbs, r_y two) summed on leveled accumulators: e is of order
+//   2^-104 and exact to about 2^-212 after its leading terms cancel, so two
+//   limbs of it suffice;
+//   r' = r + r (e + e^2): the products r e (two-limb by two-limb, TwoProd on
+//   the leading limbs) and the second-order term added to r's limbs on the
+//   levels of an L-limb accumulator: relative error of order |e|^3 + 2^-53L.
+// The products, the two parts of e and the two parts of r' are independent
+// chains (the TD / QD panel spreads them over warps).
+template <int L>
+__device__ __forceinline__ void rcp_prod(Acc<L> &P, const R<L> &px, double y0, double y1) {
+  P.zero();
+  P.add_prod1(y0, px);
+  P.add_prod1(y1, px);
+}
+
+// Re e = 1 - P_rr + P_ii (IM false), Im e = -(P_ri + P_ir) (IM true).  The
+// leading levels cancel down to about 2^-105, where one renormalisation
+// leaves its two leading limbs overlapping (the pair then misses terms of
+// order 2^-159); a second pass makes them nonoverlapping (the pair within
+// about 2^-211 of the sum).
+template <int L, bool IM>
+__device__ __forceinline__ R<L> rcp_resid_l(const Acc<L> &Pa, const Acc<L> &Pb) {
+  Acc<L> t;
+  t.zero();
+  if (!IM) t.s[0] = 1.0;
+  t.add_acc(Pa, true);
+  t.add_acc(Pb, IM);
+  R<L> e = t.result();
+  renorm_n<L>(e.x);
+  return e;
+}
+
+// part IM of r' = r + r e + r e^2 (r, e: two limbs per part)
+template <int L, bool IM>
+__device__ __forceinline__ R<L> rcp_newton(const double (&r)[4], const double (&e)[4]) {
+  const double rr0 = r[0], rr1 = r[1], ri0 = r[2], ri1 = r[3];
+  const double er0 = e[0], er1 = e[1], ei0 = e[2], ei1 = e[3];
+  Acc<L> u;
+  u.zero();
+  u.s[0] = IM ? ri0 : rr0;
+  u.s[1] = IM ? ri1 : rr1;
+  double p, q;
+  // leading products: Re: rr0 er0 - ri0 ei0, Im: rr0 ei0 + ri0 er0
+  two_prod(rr0, IM ? ei0 : er0, p, q);
+  u.template dep<2>(p);
+  u.template dep<3>(q);
+  two_prod(IM ? ri0 : flip(ri0), IM ? er0 : ei0, p, q);
+  u.template dep<2>(p);
+  u.template dep<3>(q);
+  // the remaining first-order terms and e^2 = (er0^2 - ei0^2) + 2 er0 ei0 i
+  double t = 0.0;
+  if (!IM) {
+    t = __fma_rn(rr0, er1, t);
+    t = __fma_rn(rr1, er0, t);
+    t = __fma_rn(flip(ri0), ei1, t);
+    t = __fma_rn(flip(ri1), ei0, t);
+    t = __fma_rn(rr1, er1, t);
+    t = __fma_rn(flip(ri1), ei1, t);
+  } else {
+    t = __fma_rn(rr0, ei1, t);
+    t = __fma_rn(rr1, ei0, t);
+    t = __fma_rn(ri0, er1, t);
+    t = __fma_rn(ri1, er0, t);
+    t = __fma_rn(rr1, ei1, t);
+    t = __fma_rn(ri1, er1, t);
+  }
+  const double e2r = __fma_rn(er0, er0, flip(__dmul_rn(ei0, ei0)));
+  const double e2i = __dmul_rn(__dadd_rn(er0, er0), ei0);
+  if (!IM) {
+    t = __fma_rn(rr0, e2r, t);
+    t = __fma_rn(flip(ri0), e2i, t);
+  } else {
+    t = __fma_rn(rr0, e2i, t);
+    t = __fma_rn(ri0, e2r, t);
+  }
+  u.template dep<3>(t);
+  return u.result();
+}
+
 template <int L>
 __device__ __forceinline__ Z<L> z_inv_newton(const Z<L> &p) {
   const RcpSeed s = rcp_seed(p.re.x[0], p.im.x[0]);
@@ -587,27 +668,17 @@ __device__ __forceinline__ Z<L> z_inv_newton(const Z<L> &p) {
   r.re = rcp_finish<L, false>(s, er, ei);
   r.im = rcp_finish<L, true>(s, er, ei);
   if constexpr (L >= 3) {
-    // e = 1 - p r, then r + r e, in L-limb arithmetic
-    Acc<L> t;
-    t.zero();
-    t.s[0] = 1.0;
-    t.template add_prod<true>(p.re, r.re);
-    t.template add_prod<false>(p.im, r.im);
-    const R<L> e_re = t.result();
-    t.zero();
-    t.template add_prod<true>(p.re, r.im);
-    t.template add_prod<true>(p.im, r.re);
-    const R<L> e_im = t.result();
-    Acc<L> u;
-    u.set(r.re);
-    u.template add_prod<false>(r.re, e_re);
-    u.template add_prod<true>(r.im, e_im);
-    const R<L> n_re = u.result();
-    u.set(r.im);
-    u.template add_prod<false>(r.re, e_im);
-    u.template add_prod<false>(r.im, e_re);
-    r.im = u.result();
-    r.re = n_re;
+    const double r2[4] = {r.re.x[0], r.re.x[1], r.im.x[0], r.im.x[1]};
+    Acc<L> Prr, Pii, Pri, Pir;
+    rcp_prod<L>(Prr, p.re, r2[0], r2[1]);
+    rcp_prod<L>(Pii, p.im, r2[2], r2[3]);
+    rcp_prod<L>(Pri, p.re, r2[2], r2[3]);
+    rcp_prod<L>(Pir, p.im, r2[0], r2[1]);
+    const R<L> e_re = rcp_resid_l<L, false>(Prr, Pii);
+    const R<L> e_im = rcp_resid_l<L, true>(Pri, Pir);
+    const double e2[4] = {e_re.x[0], e_re.x[1], e_im.x[0], e_im.x[1]};
+    r.re = rcp_newton<L, false>(r2, e2);
+    r.im = rcp_newton<L, true>(r2, e2);
   }
   return r;
 }

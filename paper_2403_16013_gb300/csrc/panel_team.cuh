@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(COOP_T) k_panel_team(View A, int64_t n, int64_
     // multipliers of column jc-1 are final, to the done signal it waits for
     // before publishing rows of column jc.
     // The update runs on warps 5, 6 and 7 (SMSPs 1, 2, 3); warp 4 stays
-    // off SMSP 0, whose FP64 unit carries the factor team's serial chain.
+    // off SMSP 0, whose FP64 unit carries the factor team's serial chain
+    // (measured: with warp 4 and per-component items, TD panel 94.1 ->
+    // 96.7 ms, QD 189.0 -> 187.0 ms at n = 4096).
     const int ut = tid - 160;  // warps 5..7: 0 .. 95
     for (int jc = 0; jc < nb; jc++) {
       named_sync(BAR_GO, 256);
@@ -237,43 +239,50 @@ __global__ void __launch_bounds__(COOP_T) k_panel_team(View A, int64_t n, int64_
       const int cr = has ? (int)(cand - rbeg) : -1;                    // local row of the candidate
       const int jr = (j >= rbeg && j < rend) ? (int)(j - rbeg) : -1;  // local row j
       if (w < 3) {
-        // 2. warps 0 and 1: the reciprocal 1/p = conj(p) / |p|^2 of the
-        //    candidate (SMSPs 0 and 1: Re p^2 and Im p^2 in parallel, the
-        //    real reciprocal x of |p|^2 on warp 0, then Re p x and -Im p x
-        //    in parallel); then, once the update team is done with column
+        // 2. warps 0 and 1: the reciprocal 1/p of the candidate (Newton's
+        //    method, its real and imaginary chains on SMSPs 0 and 1); then,
+        //    once the update team is done with column
         //    jc-1, warp 2 publishes the candidate row and row j, and thread 0
         //    releases the slot's flag
         if (w < 2) {
-          __shared__ double s_inv[2 * L];  // Im p^2 accumulator, then x
+          // 1/p by Newton's method (z_inv_newton): the binary64 seed and the
+          // two-limb step with the real part on warp 0 and the imaginary part
+          // on warp 1, then the L-limb step: warp 0 forms P_rr, P_ii and Re e,
+          // warp 1 P_ri, P_ir and Im e, and each its part of r'
+          __shared__ double s_e[2], s_r2[4], s_el[4];
           const bool act = has && lane == 0;
           Z<L> pv;
-          Acc<L> t;
+          RcpSeed sd;
           if (act) {
             pv = ldp(cr, jc);
-            const R<L> h = w == 0 ? pv.re : pv.im;
-            t.set_prod(h, h);
-            if (w == 1) {
-#pragma unroll
-              for (int l = 0; l < L; l++) s_inv[l] = t.s[l];
+            sd = rcp_seed(pv.re.x[0], pv.im.x[0]);
+            s_e[w] = w == 0 ? rcp_resid_re<L>(pv.re, pv.im, sd) : rcp_resid_im<L>(pv.re, pv.im, sd);
+          }
+          named_sync(BAR_RCP, 64);
+          R<L> v;
+          if (act) {
+            v = w == 0 ? rcp_finish<L, false>(sd, s_e[0], s_e[1]) : rcp_finish<L, true>(sd, s_e[0], s_e[1]);
+            s_r2[2 * w] = v.x[0];
+            s_r2[2 * w + 1] = v.x[1];
+          }
+          if constexpr (L >= 3) {
+            named_sync(BAR_RCP, 64);
+            const double r2[4] = {s_r2[0], s_r2[1], s_r2[2], s_r2[3]};
+            if (act) {
+              Acc<L> Pa, Pb;
+              rcp_prod<L>(Pa, pv.re, r2[2 * w], r2[2 * w + 1]);  // P_rr (warp 0), P_ri (warp 1)
+              rcp_prod<L>(Pb, pv.im, r2[2 - 2 * w], r2[3 - 2 * w]);  // P_ii, P_ir
+              const R<L> e = w == 0 ? rcp_resid_l<L, false>(Pa, Pb) : rcp_resid_l<L, true>(Pa, Pb);
+              s_el[2 * w] = e.x[0];
+              s_el[2 * w + 1] = e.x[1];
+            }
+            named_sync(BAR_RCP, 64);
+            if (act) {
+              const double e2[4] = {s_el[0], s_el[1], s_el[2], s_el[3]};
+              v = w == 0 ? rcp_newton<L, false>(r2, e2) : rcp_newton<L, true>(r2, e2);
             }
           }
-          named_sync(BAR_RCP, 64);
-          if (has && tid == 0) {
-            Acc<L> o;
-#pragma unroll
-            for (int l = 0; l < L; l++) o.s[l] = s_inv[l];
-            t.add_acc(o, false);
-            const R<L> x = r_recip<L>(t.result());
-#pragma unroll
-            for (int l = 0; l < L; l++) s_inv[L + l] = x.x[l];
-          }
-          named_sync(BAR_RCP, 64);
           if (act) {
-            R<L> x;
-#pragma unroll
-            for (int l = 0; l < L; l++) x.x[l] = s_inv[L + l];
-            R<L> v = r_mul<L>(w == 0 ? pv.re : pv.im, x);
-            if (w == 1) v = r_neg<L>(v);
 #pragma unroll
             for (int l = 0; l < L; l++) ws.part_rcp[(int64_t)q * 2 * L + w * L + l] = v.x[l];
           }
