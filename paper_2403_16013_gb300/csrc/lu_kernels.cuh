@@ -391,22 +391,22 @@ __global__ void __launch_bounds__(PANEL_T *PANEL_T)
 // gets a slot, numbered by a block prefix sum), then one thread applies the
 // transpositions in order as swaps of org entries (two shared-memory reads
 // and writes per swap).  Then each CTA gathers the moved rows of its
-// LASWP_C columns into shared memory and writes them back permuted.  Rows in
-// [k0, k1) are contiguous in a column (coalesced); partner rows cost one
-// sector each.  k1 - k0 <= 256 (one pivot per thread).
-constexpr int LASWP_C = 16;  // columns per CTA
+// LASWP_C columns into registers, plane by plane, and writes them back
+// permuted.  Rows in [k0, k1) are contiguous in a column (coalesced);
+// partner rows cost one sector each.  k1 - k0 <= LASWP_NB_MAX (one pivot per
+// thread).
+constexpr int LASWP_C = 16;        // columns per CTA
+constexpr int LASWP_NB_MAX = 256;  // most swaps of one launch
+constexpr int LASWP_K = 2 * LASWP_NB_MAX * LASWP_C / 256;  // moved elements a thread holds
 
-inline size_t laswp_smem(int nb) {
-  return (size_t)2 * nb * (2 * sizeof(int) + LASWP_C * sizeof(double)) + (size_t)4 * nb * sizeof(int) + 16;
-}
+inline size_t laswp_smem(int nb) { return (size_t)2 * nb * 2 * sizeof(int) + (size_t)4 * nb * sizeof(int) + 16; }
 
 template <int L>
 __global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t k0, int64_t k1, const int32_t *ipiv,
                                                       int64_t c0, int64_t c1, int64_t x0, int64_t x1) {
   const int nb = (int)(k1 - k0);
   extern __shared__ double lsm[];
-  double *vals = lsm;                                      // [2 nb][LASWP_C]
-  int *dst = reinterpret_cast<int *>(vals + (size_t)2 * nb * LASWP_C);  // [2 nb]
+  int *dst = reinterpret_cast<int *>(lsm);                 // [2 nb]
   int *org = dst + 2 * nb;                                 // [2 nb]
   int *piv = org + 2 * nb;                                 // [nb] the pivots, read once
   int *fidx = piv + nb;                                    // [nb] first pivot with the same partner row
@@ -474,23 +474,31 @@ __global__ void __launch_bounds__(256) k_laswp_gather(View A, int64_t k0, int64_
   const int T = nb + s_cnt;
   const int64_t ncols = (c1 - c0) - (x1 - x0);
   const int64_t cb = (int64_t)blockIdx.x * LASWP_C;
+  // each thread gathers up to LASWP_K (slot, column) elements of a plane into
+  // registers before it stores any of them, so that its loads are in flight
+  // together (T LASWP_C <= LASWP_K x 256 threads)
   for (int pl = 0; pl < 2 * L; pl++) {
     double *P = A.p + (int64_t)pl * A.ps;
-    for (int t = tid; t < T * LASWP_C; t += 256) {
+    double v[LASWP_K];
+#pragma unroll
+    for (int k = 0; k < LASWP_K; k++) {
+      const int t = tid + 256 * k;
       const int sl = t % T, cl = t / T;
       const int64_t cc = cb + cl;
-      if (cc < ncols && org[sl] != dst[sl]) {
+      if (t < T * LASWP_C && cc < ncols && org[sl] != dst[sl]) {
         const int64_t c = (c0 + cc < x0) ? c0 + cc : c0 + cc + (x1 - x0);
-        vals[(size_t)sl * LASWP_C + cl] = P[c * A.ld + org[sl]];
+        v[k] = P[c * A.ld + org[sl]];
       }
     }
-    __syncthreads();
-    for (int t = tid; t < T * LASWP_C; t += 256) {
+    __syncthreads();  // every row read before any is written
+#pragma unroll
+    for (int k = 0; k < LASWP_K; k++) {
+      const int t = tid + 256 * k;
       const int sl = t % T, cl = t / T;
       const int64_t cc = cb + cl;
-      if (cc < ncols && org[sl] != dst[sl]) {
+      if (t < T * LASWP_C && cc < ncols && org[sl] != dst[sl]) {
         const int64_t c = (c0 + cc < x0) ? c0 + cc : c0 + cc + (x1 - x0);
-        P[c * A.ld + dst[sl]] = vals[(size_t)sl * LASWP_C + cl];
+        P[c * A.ld + dst[sl]] = v[k];
       }
     }
     __syncthreads();
