@@ -89,6 +89,43 @@ struct Workspace {
   }
 };
 
+// A second stream forked from the caller's stream s: work issued on it after
+// fork() starts once everything issued on s before that call is done, and
+// join() makes s wait for everything issued on it so far.  The destructor
+// joins (the workspace is freed stream-ordered on s, so the side work must
+// come first on every exit path) and releases the stream and the events.
+struct SideStream {
+  cudaStream_t main = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool open = false;  // work issued on side since the last join
+  cudaError_t init(cudaStream_t s) {
+    main = s;
+    cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
+    return e;
+  }
+  cudaError_t fork() {
+    cudaError_t e = cudaEventRecord(ev_fork, main);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
+    if (e == cudaSuccess) open = true;
+    return e;
+  }
+  cudaError_t join() {
+    if (!open) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(ev_join, side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(main, ev_join, 0);
+    if (e == cudaSuccess) open = false;
+    return e;
+  }
+  ~SideStream() {
+    join();
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (side) cudaStreamDestroy(side);
+  }
+};
+
 struct Carver {  // 256-byte aligned sub-allocations of one workspace block
   char *base;
   size_t off = 0;
@@ -402,7 +439,11 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   const bool ozk = method == MCLU_METHOD_OZAKI;
   Workspace w;
   const size_t oz_need = ozk ? oz::ws_bytes<L>(n, n, nb) : 0;
-  const size_t ws_need = getrf_ws_bytes<L>(n, nb, m3) + oz_need +
+  // DD: L11^-1 formed with the sub-panels on a side stream, with an Ozaki
+  // workspace of its own (its products overlap those of the main stream)
+  const bool side_w = ozk && L == 2 && n > nb;
+  const size_t oz_side_need = side_w ? ((oz::ws_bytes<L>(nb, nb, nb) + 255) & ~(size_t)255) : 0;
+  const size_t ws_need = getrf_ws_bytes<L>(n, nb, m3) + oz_need + oz_side_need +
                          (ozk ? (((size_t)(L == 2 ? 1 : 2) * 2 * L * nb * nb * sizeof(double) + 255) & ~(size_t)255)
                               : 0);
   char *ws_base = nullptr;
@@ -414,6 +455,8 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     ws_base = (char *)w.p;
   }
   Carver cv{ws_base};
+  SideStream side;  // after w: the side stream is joined before w is freed
+  if (side_w) MCLU_TRY(side.init(s));
   PanelWS<L> ws;
   char *hdr = cv.take<char>(4 * 256);
   ws.counter = (int *)hdr;
@@ -441,6 +484,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     sumU = cv.take<double>((size_t)n * nb * L);
   }
   void *oz_ws = ozk ? (void *)cv.take<char>(oz_need) : nullptr;
+  void *oz_ws_side = side_w ? (void *)cv.take<char>(oz_side_need) : nullptr;
   // L11^-1 of the current block; for TD / QD also the scratch of its composition
   double *winv = ozk ? cv.take<double>((size_t)(L == 2 ? 1 : 2) * 2 * L * nb * nb) : nullptr;
   double *oz_tmp = winv + (size_t)2 * L * nb * nb;
@@ -501,40 +545,53 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
       // applied, its rows of L11 are final, and
       //   W[R_s, 0..s0) = -L11[R_s, ..s0) W[..s0, ..s0)   (an Ozaki product)
       //   W[R_s, 0..send) = L_ss^{-1} W[R_s, 0..send)     (W starts as I)
-      // the solve sharing the launch of the block solve for the U rows.
+      // the row block's solve.  These steps read only the rows R_s of the
+      // block's columns (final once R_s's swaps are applied: later swaps
+      // move rows below R_s) and W, and only U12 = W A12 below needs W: they
+      // run on a side stream forked after the swaps, beside the main
+      // stream's block solve and product of the same sub-panel.  The next
+      // sub-panel's cooperative panel joins it first, so that the side's
+      // CTAs do not hold SMs that the panel's grid is waiting for; the last
+      // row block overlaps the block's swaps and U12 joins it.  Measured at
+      // n = 4096: TRSM (with the waits at the joins) 8.4 -> 6.9 ms, LU +
+      // solve 92.1 -> 90.8 ms; joined at U12 only, TRSM 5.0 ms but the panel
+      // 37.6 -> 39.9 ms (90.9 ms).
       // (DD only: with the 16-column sub-panels of TD and QD the eight row
       // blocks cost more than the composition below; measured at n = 4096:
       // TRSM 21.1 -> 24.1 ms (TD), 30.3 -> 33.2 ms (QD), DD 12.6 -> 10.1 ms)
       const bool mkw = jend < n && L == 2;
       View Wb{winv, jb, jb * jb};
-      if (mkw) {
-        k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(Wb, jb);
-        MCLU_LAUNCHED();
-      }
       for (int64_t s0 = j0; s0 < jend; s0 += sbw) {
         const int64_t send = std::min<int64_t>(s0 + sbw, jend), sb = send - s0;
+        if (mkw && s0 > j0) {
+          ProfScope ps(PK_TRSM, s);
+          MCLU_TRY(side.join());
+        }
         int rc = panel(s0, send);
         if (rc) return rc;
         rc = laswp(s0, send, j0, jend, s0, send);  // the block's other columns, in one launch
         if (rc) return rc;
-        if (mkw && s0 > j0) {
-          ProfScope ps(PK_TRSM, s);
-          rc = oz::gemm<L>(true, View{Ap + j0 * lda + s0, lda, lda * n}, Wb, View{winv + (s0 - j0), jb, jb * jb}, sb,
-                           s0 - j0, s0 - j0, oz_ws, oz_status, s, note_launch, Se);
+        if (mkw) {
+          MCLU_TRY(side.fork());
+          if (s0 == j0) {  // W starts as I (the previous block's U12 is done)
+            k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, side.side>>>(Wb, jb);
+            MCLU_LAUNCHED();
+          } else {
+            rc = oz::gemm<L>(true, View{Ap + j0 * lda + s0, lda, lda * n}, Wb, View{winv + (s0 - j0), jb, jb * jb},
+                             sb, s0 - j0, s0 - j0, oz_ws_side, oz_status, side.side, note_launch, Se);
+            if (rc) return rc;
+          }
+          rc = launch_lsolve<L>(side.side, A, s0, (int)sb, Wb, send - j0, s0 - j0);
           if (rc) return rc;
         }
         if (send < jend) {
           ProfScope ps(PK_OTHER, s);
           View U{Ap + send * lda, lda, lda * n};  // rows s0.., columns send..jend
-          rc = launch_lsolve<L>(s, A, s0, (int)sb, U, jend - send, s0, Wb, mkw ? send - j0 : 0, s0 - j0);
+          rc = launch_lsolve<L>(s, A, s0, (int)sb, U, jend - send, s0);
           if (rc) return rc;
           rc = oz::gemm<L>(true, View{Ap + s0 * lda + send, lda, lda * n}, View{Ap + send * lda + s0, lda, lda * n},
                            View{Ap + send * lda + send, lda, lda * n}, n - send, jend - send, sb, oz_ws, oz_status, s,
                            note_launch, Se);
-          if (rc) return rc;
-        } else if (mkw) {
-          ProfScope ps(PK_TRSM, s);
-          rc = launch_lsolve<L>(s, A, s0, (int)sb, Wb, send - j0, s0 - j0);
           if (rc) return rc;
         }
       }
@@ -556,7 +613,9 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
           // above), as an Ozaki product written in place (the operands are
           // sliced before the product is stored).
           View W{winv, jb, jb * jb};
-          if (L != 2) {
+          if (L == 2) {
+            MCLU_TRY(side.join());  // W, formed on the side stream
+          } else {
             // W by the block solve on the identity (one 32-column sub-panel),
             // else the inverses of the 32 x 32 diagonal blocks in one launch
             // and 2 x 2 block inversion upwards: inv([[P, 0], [C, Q]]) has the
