@@ -442,7 +442,9 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   // DD: L11^-1 formed with the sub-panels on a side stream, with an Ozaki
   // workspace of its own (its products overlap those of the main stream)
   const bool side_w = ozk && L == 2 && n > nb;
-  const size_t oz_side_need = side_w ? ((oz::ws_bytes<L>(nb, nb, nb) + 255) & ~(size_t)255) : 0;
+  const size_t oz_side_need = side_w ? ((oz::ws_bytes<L>(nb, nb, nb) + 255) & ~(size_t)255) +
+                                           ((2 * L * (size_t)sbw * nb * sizeof(double) + 255) & ~(size_t)255)
+                                     : 0;
   const size_t ws_need = getrf_ws_bytes<L>(n, nb, m3) + oz_need + oz_side_need +
                          (ozk ? (((size_t)(L == 2 ? 1 : 2) * 2 * L * nb * nb * sizeof(double) + 255) & ~(size_t)255)
                               : 0);
@@ -484,7 +486,8 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
     sumU = cv.take<double>((size_t)n * nb * L);
   }
   void *oz_ws = ozk ? (void *)cv.take<char>(oz_need) : nullptr;
-  void *oz_ws_side = side_w ? (void *)cv.take<char>(oz_side_need) : nullptr;
+  void *oz_ws_side = side_w ? (void *)cv.take<char>(oz::ws_bytes<L>(nb, nb, nb)) : nullptr;
+  double *tbuf = side_w ? cv.take<double>(2 * L * (size_t)sbw * nb) : nullptr;  // L11[R_s, ..) W of a sub-panel
   // L11^-1 of the current block; for TD / QD also the scratch of its composition
   double *winv = ozk ? cv.take<double>((size_t)(L == 2 ? 1 : 2) * 2 * L * nb * nb) : nullptr;
   double *oz_tmp = winv + (size_t)2 * L * nb * nb;
@@ -542,28 +545,39 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
       //
       // When a trailing part follows, W = L11^{-1} is formed on the way, one
       // row block per sub-panel R_s: once R_s is factored and its swaps are
-      // applied, its rows of L11 are final, and
-      //   W[R_s, 0..s0) = -L11[R_s, ..s0) W[..s0, ..s0)   (an Ozaki product)
-      //   W[R_s, 0..send) = L_ss^{-1} W[R_s, 0..send)     (W starts as I)
-      // the row block's solve.  These steps read only the rows R_s of the
-      // block's columns (final once R_s's swaps are applied: later swaps
-      // move rows below R_s) and W, and only U12 = W A12 below needs W: they
-      // run on a side stream forked after the swaps, beside the main
-      // stream's block solve and product of the same sub-panel.  The next
-      // sub-panel's cooperative panel joins it first, so that the side's
-      // CTAs do not hold SMs that the panel's grid is waiting for; the last
-      // row block overlaps the block's swaps and U12 joins it.  Measured at
-      // n = 4096: TRSM (with the waits at the joins) 8.4 -> 6.9 ms, LU +
-      // solve 92.1 -> 90.8 ms; joined at U12 only, TRSM 5.0 ms but the panel
-      // 37.6 -> 39.9 ms (90.9 ms).
+      // applied, its rows of L11 are final, and (W starts as I)
+      //   W[R_s, R_s]   = L_ss^{-1}                       (block solve on I)
+      //   T             = L11[R_s, ..s0) W[..s0, ..s0)    (Ozaki product)
+      //   W[R_s, 0..s0) = -L_ss^{-1} T                    (Ozaki product)
+      // L_ss^{-1} shares the launch of the block solve of the sub-panel's U
+      // rows (the same triangle and chain).  The products read only rows R_s
+      // of the block's columns (final once R_s's swaps are applied: later
+      // swaps move rows below R_s) and W, and only U12 = W A12 below needs
+      // W, so they run on a side stream: T forked after the swaps, beside the
+      // block solve; the second product after the block solve, beside the
+      // sub-panel's Ozaki product.  The next sub-panel's cooperative panel
+      // joins the side stream first, so that its CTAs do not hold SMs the
+      // panel's grid waits for; U12 joins the last row block.  Measured at
+      // n = 4096 (DD), TRSM with the waits at the joins: 8.4 ms with W[R_s,
+      // 0..s0) by one product and the row block's solve in the main stream;
+      // 6.9 ms with those two on the side stream (a chain of 32 dependent
+      // steps there, longer than the main stream's work beside it, so its
+      // joins waited); joined at U12 only, TRSM 5.0 ms but the panel 37.6
+      // -> 39.9 ms (its grid waited for the side stream's CTAs).
       // (DD only: with the 16-column sub-panels of TD and QD the eight row
       // blocks cost more than the composition below; measured at n = 4096:
       // TRSM 21.1 -> 24.1 ms (TD), 30.3 -> 33.2 ms (QD), DD 12.6 -> 10.1 ms)
       const bool mkw = jend < n && L == 2;
       View Wb{winv, jb, jb * jb};
+      View Tv{tbuf, sbw, (int64_t)sbw * nb};
+      if (mkw) {  // W = I (the previous block's U12 is done)
+        k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(Wb, jb);
+        MCLU_LAUNCHED();
+      }
       for (int64_t s0 = j0; s0 < jend; s0 += sbw) {
         const int64_t send = std::min<int64_t>(s0 + sbw, jend), sb = send - s0;
-        if (mkw && s0 > j0) {
+        const int64_t wc = s0 - j0;  // columns of W left of R_s
+        if (mkw && wc > 0) {
           ProfScope ps(PK_TRSM, s);
           MCLU_TRY(side.join());
         }
@@ -571,24 +585,27 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
         if (rc) return rc;
         rc = laswp(s0, send, j0, jend, s0, send);  // the block's other columns, in one launch
         if (rc) return rc;
-        if (mkw) {
+        if (mkw && wc > 0) {  // T = L11[R_s, ..s0) W[..s0, ..s0)
           MCLU_TRY(side.fork());
-          if (s0 == j0) {  // W starts as I (the previous block's U12 is done)
-            k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, side.side>>>(Wb, jb);
-            MCLU_LAUNCHED();
-          } else {
-            rc = oz::gemm<L>(true, View{Ap + j0 * lda + s0, lda, lda * n}, Wb, View{winv + (s0 - j0), jb, jb * jb},
-                             sb, s0 - j0, s0 - j0, oz_ws_side, oz_status, side.side, note_launch, Se);
-            if (rc) return rc;
-          }
-          rc = launch_lsolve<L>(side.side, A, s0, (int)sb, Wb, send - j0, s0 - j0);
+          rc = oz::gemm<L>(false, View{Ap + j0 * lda + s0, lda, lda * n}, Wb, Tv, sb, wc, wc, oz_ws_side, oz_status,
+                           side.side, note_launch, Se);
+          if (rc) return rc;
+        }
+        {  // the U rows of the block's columns right of R_s, and W[R_s, R_s] = L_ss^{-1}
+          ProfScope ps(send < jend ? PK_OTHER : PK_TRSM, s);
+          View U{Ap + send * lda, lda, lda * n};  // rows s0.., columns send..jend
+          rc = launch_lsolve<L>(s, A, s0, (int)sb, U, jend - send, s0, View{winv + wc * jb, jb, jb * jb},
+                                mkw ? sb : 0, wc);
+          if (rc) return rc;
+        }
+        if (mkw && wc > 0) {  // W[R_s, 0..s0) = -L_ss^{-1} T
+          MCLU_TRY(side.fork());
+          rc = oz::gemm<L>(true, View{winv + wc * jb + wc, jb, jb * jb}, Tv, View{winv + wc, jb, jb * jb}, sb, wc, sb,
+                           oz_ws_side, oz_status, side.side, note_launch, Se);
           if (rc) return rc;
         }
         if (send < jend) {
           ProfScope ps(PK_OTHER, s);
-          View U{Ap + send * lda, lda, lda * n};  // rows s0.., columns send..jend
-          rc = launch_lsolve<L>(s, A, s0, (int)sb, U, jend - send, s0);
-          if (rc) return rc;
           rc = oz::gemm<L>(true, View{Ap + s0 * lda + send, lda, lda * n}, View{Ap + send * lda + s0, lda, lda * n},
                            View{Ap + send * lda + send, lda, lda * n}, n - send, jend - send, sb, oz_ws, oz_status, s,
                            note_launch, Se);
