@@ -439,14 +439,14 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   const bool ozk = method == MCLU_METHOD_OZAKI;
   Workspace w;
   const size_t oz_need = ozk ? oz::ws_bytes<L>(n, n, nb) : 0;
-  // DD: L11^-1 formed with the sub-panels on a side stream, with an Ozaki
+  // L11^-1 formed with the sub-panels on a side stream, with an Ozaki
   // workspace of its own (its products overlap those of the main stream)
-  const bool side_w = ozk && L == 2 && n > nb;
+  const bool side_w = ozk && n > nb;
   const size_t oz_side_need = side_w ? ((oz::ws_bytes<L>(nb, nb, nb) + 255) & ~(size_t)255) +
                                            ((2 * L * (size_t)sbw * nb * sizeof(double) + 255) & ~(size_t)255)
                                      : 0;
   const size_t ws_need = getrf_ws_bytes<L>(n, nb, m3) + oz_need + oz_side_need +
-                         (ozk ? (((size_t)(L == 2 ? 1 : 2) * 2 * L * nb * nb * sizeof(double) + 255) & ~(size_t)255)
+                         (ozk ? (((size_t)2 * L * nb * nb * sizeof(double) + 255) & ~(size_t)255)
                               : 0);
   char *ws_base = nullptr;
   if (ext_ws) {
@@ -489,8 +489,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   void *oz_ws_side = side_w ? (void *)cv.take<char>(oz::ws_bytes<L>(nb, nb, nb)) : nullptr;
   double *tbuf = side_w ? cv.take<double>(2 * L * (size_t)sbw * nb) : nullptr;  // L11[R_s, ..) W of a sub-panel
   // L11^-1 of the current block; for TD / QD also the scratch of its composition
-  double *winv = ozk ? cv.take<double>((size_t)(L == 2 ? 1 : 2) * 2 * L * nb * nb) : nullptr;
-  double *oz_tmp = winv + (size_t)2 * L * nb * nb;
+  double *winv = ozk ? cv.take<double>((size_t)2 * L * nb * nb) : nullptr;
   int *oz_status = ws.zflag + 1;  // spare word of the header block
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));
   MCLU_TRY(cudaMemsetAsync(cw.rcp_flag, 0, (size_t)2 * COOP_GMAX * sizeof(int), s));
@@ -563,11 +562,12 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
       // 6.9 ms with those two on the side stream (a chain of 32 dependent
       // steps there, longer than the main stream's work beside it, so its
       // joins waited); joined at U12 only, TRSM 5.0 ms but the panel 37.6
-      // -> 39.9 ms (its grid waited for the side stream's CTAs).
-      // (DD only: with the 16-column sub-panels of TD and QD the eight row
-      // blocks cost more than the composition below; measured at n = 4096:
-      // TRSM 21.1 -> 24.1 ms (TD), 30.3 -> 33.2 ms (QD), DD 12.6 -> 10.1 ms)
-      const bool mkw = jend < n && L == 2;
+      // -> 39.9 ms (its grid waited for the side stream's CTAs).  TD and QD
+      // (16-column sub-panels) formed W after the block, from the 32 x 32
+      // diagonal inverses by 2 x 2 block inversion (six Ozaki products on
+      // the main stream); the row blocks on the side stream measured TRSM
+      // TD 17.7 -> 8.3 ms, QD 27.4 -> 12.7 ms at n = 4096.
+      const bool mkw = jend < n;
       View Wb{winv, jb, jb * jb};
       View Tv{tbuf, sbw, (int64_t)sbw * nb};
       if (mkw) {  // W = I (the previous block's U12 is done)
@@ -626,44 +626,11 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
           int rc = launch_lsolve<L>(s, A, j0, (int)jb, A12, n2, j0);
           if (rc) return rc;
         } else {
-          // U12 = W A12 with W = L11^{-1} (DD: formed with the sub-panels
-          // above), as an Ozaki product written in place (the operands are
-          // sliced before the product is stored).
+          // U12 = W A12 with W = L11^{-1} (formed with the sub-panels above,
+          // on the side stream), as an Ozaki product written in place (the
+          // operands are sliced before the product is stored).
           View W{winv, jb, jb * jb};
-          if (L == 2) {
-            MCLU_TRY(side.join());  // W, formed on the side stream
-          } else {
-            // W by the block solve on the identity (one 32-column sub-panel),
-            // else the inverses of the 32 x 32 diagonal blocks in one launch
-            // and 2 x 2 block inversion upwards: inv([[P, 0], [C, Q]]) has the
-            // lower-left block -inv(Q) C inv(P), two Ozaki products per pair
-            k_identity<L><<<(unsigned)cdiv(jb * jb, 256), 256, 0, s>>>(W, jb);
-            MCLU_LAUNCHED();
-            constexpr int SB = oz::NB_MAX;  // 32
-            if (jb <= SB) {
-              int rc0 = launch_lsolve<L>(s, A, j0, (int)jb, W, jb, 0);
-              if (rc0) return rc0;
-            } else {
-              const int nsb = (int)cdiv(jb, SB);
-              k_lsolve4<L><<<dim3(SB, nsb), dim3(SB, 4), lsolve4_smem<L>(SB), s>>>(A, j0, (int)jb, W, 0, SB,
-                                                                                   View{nullptr, 0, 0}, INT64_MAX, 0);
-              MCLU_LAUNCHED();
-              View Tm{oz_tmp, nb, (int64_t)nb * nb};  // scratch for C inv(P)
-              for (int64_t h = SB; h < jb; h *= 2) {
-                for (int64_t a = 0; a + h < jb; a += 2 * h) {
-                  const int64_t hb = std::min<int64_t>(h, jb - a - h);  // rows of Q
-                  View Cv{Ap + (j0 + a) * lda + (j0 + a + h), lda, lda * n};  // L rows a+h.., columns a..
-                  View Pi{W.p + a * W.ld + a, W.ld, W.ps};
-                  View Qi{W.p + (a + h) * W.ld + (a + h), W.ld, W.ps};
-                  View X21{W.p + a * W.ld + (a + h), W.ld, W.ps};
-                  int rc1 = oz::gemm<L>(false, Cv, Pi, Tm, hb, h, h, oz_ws, oz_status, s, note_launch, Se);
-                  if (rc1) return rc1;
-                  rc1 = oz::gemm<L>(true, Qi, Tm, X21, hb, h, hb, oz_ws, oz_status, s, note_launch, Se);
-                  if (rc1) return rc1;
-                }
-              }
-            }
-          }
+          MCLU_TRY(side.join());
           int rc = oz::gemm<L>(false, W, View{Ap + jend * lda + j0, lda, lda * n}, View{Ap + jend * lda + j0, lda, lda * n},
                                jb, n2, jb, oz_ws, oz_status, s, note_launch, Se);
           if (rc) return rc;
