@@ -411,7 +411,9 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   int Se = 0;  // Ozaki slices per operand (0: the precision's default)
   // Ozaki: sub-panel width; measured at n = 4096: 32 for DD (16: the panel
   // 43.8 -> 39.9 ms, the updates between sub-panels 10.8 -> 19.0 ms), 16 for
-  // TD and QD (LU + solve +2% and +7.6% over 32)
+  // TD and QD (LU + solve +2% and +7.6% over 32); again with L11^-1 formed
+  // on the side stream: DD 88.6 ms (16: 96.9, 24: 92.9), TD 223.9 ms (32:
+  // 240.6), QD 392.9 ms (32: 450.0)
   int sbw = L == 2 ? oz::NB_MAX : oz::NB_MAX / 2;
   if (opts) {
     if (opts->nb < 0 || opts->nb > 256) return -6;
