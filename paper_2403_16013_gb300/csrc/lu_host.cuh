@@ -201,7 +201,7 @@ int launch_lsolve(cudaStream_t s, View A, int64_t k0, int bs, View X, int64_t nc
   if (ncols + ncols2 == 0) return 0;
   const int RT = (bs + 31) / 32 * 32;
   if (bs <= 64 || (L >= 3 && bs <= 128)) {
-    k_lsolve4<L><<<(unsigned)(ncols + ncols2), dim3(RT, 4), lsolve4_smem<L>(RT), s>>>(A, k0, bs, X, xrow0, 0, X2,
+    k_lsolve4<L><<<(unsigned)(ncols + ncols2), dim3(RT, 4), lsolve4_smem<L>(RT), s>>>(A, k0, bs, X, xrow0, X2,
                                                                                       ncols, xrow2);
     MCLU_LAUNCHED();
     return 0;
@@ -490,7 +490,7 @@ int getrf(int64_t n, double *Ap, int64_t lda, int32_t *ipiv, int32_t *info, cons
   void *oz_ws = ozk ? (void *)cv.take<char>(oz_need) : nullptr;
   void *oz_ws_side = side_w ? (void *)cv.take<char>(oz::ws_bytes<L>(nb, nb, nb)) : nullptr;
   double *tbuf = side_w ? cv.take<double>(2 * L * (size_t)sbw * nb) : nullptr;  // L11[R_s, ..) W of a sub-panel
-  // L11^-1 of the current block; for TD / QD also the scratch of its composition
+  // L11^-1 of the current block
   double *winv = ozk ? cv.take<double>((size_t)2 * L * nb * nb) : nullptr;
   int *oz_status = ws.zflag + 1;  // spare word of the header block
   MCLU_TRY(cudaMemsetAsync(hdr, 0, 3 * 256, s));

@@ -646,15 +646,12 @@ __global__ void k_tri_block(View A, int64_t k0, int bs, View X, int64_t ncols, c
 // four FP64 units), and x_k = (P0 + P1) + i (P2 + P3) is formed when row k
 // is final.  Column k of T is streamed through registers and shared memory
 // ahead of its step (below).  Block (bs rounded up to 32, 4), bs <= 128.
-// ystep > 0: the grid's y index selects the diagonal block at offset
-// y ystep of a bs-row block (its rows, its columns of X), bs <= ystep rows
-// each: the diagonal-block inverses of a larger triangle in one launch.
 // Columns blockIdx.x >= ncol1 are columns blockIdx.x - ncol1 of a second
 // right-hand side X2 (rows xrow2 ..): two solves with the same triangle in
 // one launch.
 template <int L>
-__global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, View X, int64_t xrow0, int ystep,
-                                                 View X2, int64_t ncol1, int64_t xrow2) {
+__global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, View X, int64_t xrow0, View X2,
+                                                 int64_t ncol1, int64_t xrow2) {
   const int r = threadIdx.x, p = threadIdx.y;
   const int RT = blockDim.x;
   const int tid = p * RT + r;
@@ -663,14 +660,6 @@ __global__ void __launch_bounds__(512) k_lsolve4(View A, int64_t k0, int bs, Vie
     X = X2;
     c -= ncol1;
     xrow0 = xrow2;
-  }
-  if (ystep > 0) {
-    const int koff = (int)blockIdx.y * ystep;
-    bs = min(ystep, bs - koff);
-    if ((int)blockIdx.x >= bs) return;  // whole CTA: beyond this block's columns
-    k0 += koff;
-    xrow0 += koff;
-    c += koff;
   }
   extern __shared__ double lsm4[];
   double *col = lsm4;                              // [3][RT][2L]: column k of T
