@@ -88,6 +88,11 @@ int zgetrf_qd(int64_t n, double *A, int64_t lda, int32_t *ipiv, void *stream);
  *         U[k,k] (LAPACK convention); < 0 only if a tensor-core pipeline
  *         wait of MCLU_METHOD_OZAKI timed out (results invalid)
  *   opts  host pointer or NULL (defaults)
+ * With MCLU_METHOD_OZAKI and n > nb, part of the work (the row blocks of
+ * L11^-1, two small Ozaki products per sub-panel) runs on a stream the call
+ * creates and destroys itself, forked from `stream` with events and joined
+ * back to it before the call's last work on `stream`: to the caller the call
+ * is ordered on `stream` like any other.
  */
 int zgetrf_dd_ex(int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info, const mclu_opts *opts,
                  void *stream);
